@@ -1,0 +1,158 @@
+/*
+ * cdct.h -- C ABI of the GB300 library for the blockwise 2-D DCT
+ * approximations of arXiv 2207.11638 ("DCT Approximations Based on Chen's
+ * Factorization").
+ *
+ * The library applies, to every N x N block of a batch of images, the
+ * JPEG-like pipeline of Sec. 5.1:
+ *
+ *     forward   B  = C A C^{-1}            (C = S T, Sec. 3.1 / Sec. 6.1)
+ *     zonal     keep the first r coefficients of B in zig-zag order
+ *     inverse   A' = C^{-1} B C
+ *     error     PSNR of A' against A
+ *
+ * with T one of the multiplierless matrices
+ *     T~_N  (CDCT_TILDE, sign approximation, Eq. 4 and Eq. app_N),
+ *     T^_N  (CDCT_HAT,   round approximation, Eq. 5 and Eq. app_N),
+ * for N = 8, 16, 32 (16 and 32 by the JAM recursion of Sec. 6.1), or the
+ * exact 8-point DCT-II (CDCT_EXACT, Chen's factorization Eq. 3).
+ *
+ * Integer variants never form B: they compute the integer coefficients
+ * Y = T A U with U = N T^{-1} (an integer matrix), keep the zonal mask on Y
+ * (the diagonal scale S cancels exactly in A'), and reconstruct
+ * A' = (U Ym T) / N^2.  All integer stages are int32 adds and shifts; the
+ * float reconstruction is the correctly rounded value of that rational.
+ * With flag CDCT_CONV_TRANSPOSE the usual B = C A C^T, A' = C^{-1} B C^{-T}
+ * is used instead (Y = T A T^T, A' = U Ym U^T / N^2).
+ *
+ * Conventions for every entry point:
+ *  - Pointers to pixels, coefficients, reconstructions, PSNR outputs and
+ *    workspaces are DEVICE pointers on the current CUDA device; the caller
+ *    allocates and owns them.  A plan owns only host-side tables.
+ *  - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  No entry point synchronises.
+ *  - Images: rows of `width` pixels `pitch` elements apart; `batch` images
+ *    `batch_stride` elements apart.  Sizes not divisible by N are padded by
+ *    replicating the last row / column; outputs and the error cover the
+ *    original width x height only.  CDCT_I16 pixels must lie in [-255, 255]
+ *    (residuals of 8-bit frames): that range bounds every int32 intermediate.
+ *  - Coefficient buffers are block-major: [batch][by][bx][N][N] (row i,
+ *    column j of each block), int32 for CDCT_TILDE / CDCT_HAT, float for
+ *    CDCT_EXACT.  Kept coefficients are [batch][by][bx][r] in zig-zag order.
+ *  - Errors: every call returns a cdct_status.  Invalid arguments return
+ *    CDCT_EINVAL before anything is launched; cdct_last_error() then gives a
+ *    message (per calling thread).  CDCT_ECUDA reports a failed launch.
+ */
+#ifndef CDCT_H
+#define CDCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cdct_plan_s* cdct_plan;
+
+typedef enum {
+  CDCT_OK = 0,
+  CDCT_EINVAL = 1,        /* invalid argument; nothing launched */
+  CDCT_ENOMEM = 2,        /* host allocation failed */
+  CDCT_ECUDA = 3,         /* a CUDA launch or call failed */
+  CDCT_EUNSUPPORTED = 4,  /* valid but not provided (e.g. EXACT with N != 8) */
+  CDCT_ETIMEOUT = 5       /* reserved for bounded device waits */
+} cdct_status;
+
+typedef enum {
+  CDCT_EXACT = 0,  /* exact DCT-II, N = 8 only, float32 via Eq. 3 */
+  CDCT_TILDE = 1,  /* T~_N: sign() of the Chen constants (Eq. 4, Eq. app_N) */
+  CDCT_HAT = 2     /* T^_N: round() of the Chen constants (Eq. 5, Eq. app_N) */
+} cdct_variant;
+
+typedef enum { CDCT_U8 = 0, CDCT_I16 = 1 } cdct_dtype;
+
+/* plan flags */
+#define CDCT_CONV_PAPER 0u      /* B = C A C^{-1}, A' = C^{-1} B C (Sec. 5.1) */
+#define CDCT_CONV_TRANSPOSE 1u  /* B = C A C^T,  A' = C^{-1} B C^{-T} */
+
+/* which matrix cdct_matrix() returns */
+#define CDCT_MATRIX_T 0       /* T_N (N x N, row-major); 2 C_8 for EXACT */
+#define CDCT_MATRIX_U 1       /* U_N = N T_N^{-1} (N x N); 4 C_8^T for EXACT */
+#define CDCT_MATRIX_S 2       /* diag(S_N) = diag(T T^T)^{-1/2} (N values) */
+#define CDCT_MATRIX_ZIGZAG 3  /* zig-zag position of (i, j) (N x N) */
+
+/* A batch of images in device memory. */
+typedef struct {
+  const void* data;       /* first pixel of image 0 (device) */
+  int32_t dtype;          /* cdct_dtype */
+  int32_t width, height;  /* >= 1 */
+  int64_t pitch;          /* elements between rows, >= width */
+  int32_t batch;          /* number of images, >= 1 */
+  int64_t batch_stride;   /* elements between images, >= pitch * height (ignored if batch == 1) */
+} cdct_image;
+
+/* Create a plan for block size n (8, 16, 32) and a variant; flags is
+ * CDCT_CONV_PAPER or CDCT_CONV_TRANSPOSE.  *out receives the plan, which
+ * the caller releases with cdct_plan_destroy.  Plans are immutable and may
+ * be shared between threads. */
+cdct_status cdct_plan_create(int n, int variant, uint32_t flags, cdct_plan* out);
+cdct_status cdct_plan_destroy(cdct_plan plan);
+
+/* Number of N x N blocks of `in` after padding (batch * nby * nbx). */
+cdct_status cdct_block_count(cdct_plan plan, const cdct_image* in, int64_t* n_blocks);
+
+/* Bytes of device workspace the PSNR-producing calls need for `in`. */
+cdct_status cdct_workspace_size(cdct_plan plan, const cdct_image* in, size_t* bytes);
+
+/* Forward transform (Sec. 5.1): coeff = Y = T A U per block (int32; float B
+ * for EXACT), block-major, cdct_block_count() * N * N elements. */
+cdct_status cdct_forward(cdct_plan plan, const cdct_image* in, void* coeff, void* stream);
+
+/* Zonal retention (Sec. 5.1): in place, zero every coefficient whose
+ * zig-zag position is >= r (1 <= r <= N*N).  Optional outputs (NULL to skip):
+ * `scaled` = B (float, same layout): diag(s) Y diag(s)^{-1} / N (paper
+ * convention) or diag(s) Y diag(s) (transpose), s = diag(S_N) of Sec. 3.1;
+ * `kept` = the first r coefficients of each block in zig-zag order. */
+cdct_status cdct_zonal(cdct_plan plan, int r, void* coeff, int64_t n_blocks, float* scaled,
+                       void* kept, void* stream);
+
+/* Inverse transform (Sec. 5.1): recon = (U Ym T) / N^2 for the original
+ * width x height of each image; recon rows recon_pitch floats apart, images
+ * recon_batch_stride floats apart. */
+cdct_status cdct_inverse(cdct_plan plan, const void* coeff, int32_t width, int32_t height,
+                         int32_t batch, float* recon, int64_t recon_pitch,
+                         int64_t recon_batch_stride, void* stream);
+
+/* PSNR (Sec. 5.1): psnr_db[b] = 10 log10(255^2 / MSE_b) over the original
+ * pixels of image b (+inf when MSE_b = 0).  psnr_db is a device array of
+ * `ref->batch` doubles; workspace needs cdct_workspace_size() bytes.  The
+ * reduction order is fixed, so results are reproducible bit for bit. */
+cdct_status cdct_psnr(const cdct_image* ref, const float* recon, int64_t recon_pitch,
+                      int64_t recon_batch_stride, double* psnr_db, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Fused forward -> zonal(r) -> inverse -> PSNR in one pass over the pixels.
+ * recon as for cdct_inverse; kept (NULL to skip) as for cdct_zonal; psnr_db
+ * (NULL to skip) as for cdct_psnr, which then needs the workspace. */
+cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, float* recon,
+                               int64_t recon_pitch, int64_t recon_batch_stride, void* kept,
+                               double* psnr_db, void* workspace, size_t workspace_bytes,
+                               void* stream);
+
+/* Host copy of a plan matrix (CDCT_MATRIX_*), computed by running the
+ * library's own butterflies on unit vectors.  `out` is host memory of N*N
+ * doubles (N for CDCT_MATRIX_S). */
+cdct_status cdct_matrix(cdct_plan plan, int which, double* out);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cdct_last_error(void);
+
+/* Library version string. */
+const char* cdct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDCT_H */

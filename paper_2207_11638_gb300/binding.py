@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libcdct.so (include/cdct.h).
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library.  PyTorch provides device memory and the current stream.  There is
+no CPU fallback: if the library is missing or fails to load, importing the
+binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcdct.so")
+
+CDCT_OK, CDCT_EINVAL, CDCT_ENOMEM, CDCT_ECUDA, CDCT_EUNSUPPORTED, CDCT_ETIMEOUT = range(6)
+VARIANTS = {"exact": 0, "tilde": 1, "hat": 2}
+CONVS = {"paper": 0, "transpose": 1}
+DTYPES = {"u8": 0, "i16": 1}
+MATRIX_T, MATRIX_U, MATRIX_S, MATRIX_ZIGZAG = range(4)
+
+# every symbol include/cdct.h declares
+EXPORTS = (
+    "cdct_plan_create", "cdct_plan_destroy", "cdct_block_count", "cdct_workspace_size",
+    "cdct_forward", "cdct_zonal", "cdct_inverse", "cdct_psnr", "cdct_fwd_zonal_inv",
+    "cdct_matrix", "cdct_last_error", "cdct_version",
+)
+
+
+class CdctImage(ctypes.Structure):
+    _fields_ = [
+        ("data", ctypes.c_void_p),
+        ("dtype", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("pitch", ctypes.c_int64),
+        ("batch", ctypes.c_int32),
+        ("batch_stride", ctypes.c_int64),
+    ]
+
+
+class CdctError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cdct status {status}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2207_11638_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    img_p = ctypes.POINTER(CdctImage)
+    sig = {
+        "cdct_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(vp)]),
+        "cdct_plan_destroy": (ctypes.c_int, [vp]),
+        "cdct_block_count": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i64)]),
+        "cdct_workspace_size": (ctypes.c_int, [vp, img_p, ctypes.POINTER(sz)]),
+        "cdct_forward": (ctypes.c_int, [vp, img_p, vp, vp]),
+        "cdct_zonal": (ctypes.c_int, [vp, ctypes.c_int, vp, i64, vp, vp, vp]),
+        "cdct_inverse": (ctypes.c_int, [vp, vp, i32, i32, i32, vp, i64, i64, vp]),
+        "cdct_psnr": (ctypes.c_int, [img_p, vp, i64, i64, vp, vp, sz, vp]),
+        "cdct_fwd_zonal_inv": (ctypes.c_int, [vp, img_p, ctypes.c_int, vp, i64, i64, vp, vp, vp, sz, vp]),
+        "cdct_matrix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "cdct_last_error": (ctypes.c_char_p, []),
+        "cdct_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def check(status: int) -> None:
+    if status != CDCT_OK:
+        raise CdctError(status, lib().cdct_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+# torch-facing helpers (torch is imported lazily: the C ABI needs none of it)
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def image_desc(t) -> CdctImage:
+    """Descriptor of a CUDA tensor [H, W] or [B, H, W] (uint8 or int16, unit column stride)."""
+    torch = _torch()
+    if not t.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    if t.dtype == torch.uint8:
+        dt = 0
+    elif t.dtype == torch.int16:
+        dt = 1
+    else:
+        raise ValueError("image dtype must be uint8 or int16")
+    if t.dim() == 2:
+        t3 = t.unsqueeze(0)
+    elif t.dim() == 3:
+        t3 = t
+    else:
+        raise ValueError("image must be [H, W] or [B, H, W]")
+    if t3.stride(2) != 1:
+        raise ValueError("image rows must be contiguous")
+    b, h, w = t3.shape
+    return CdctImage(t3.data_ptr(), dt, w, h, t3.stride(1), b, t3.stride(0) if b > 1 else h * t3.stride(1))
+
+
+class Plan:
+    """A transform plan: block size N, variant and 2-D convention (Sec. 5.1)."""
+
+    def __init__(self, n: int, variant: str = "hat", conv: str = "paper"):
+        self.n, self.variant, self.conv = n, variant, conv
+        h = ctypes.c_void_p()
+        check(lib().cdct_plan_create(n, VARIANTS[variant], CONVS[conv], ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _LIB is not None:
+            _LIB.cdct_plan_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- host tables ---------------------------------------------------------
+    def matrix(self, which: int):
+        import numpy as np
+        n = self.n
+        size = n if which == MATRIX_S else n * n
+        buf = (ctypes.c_double * size)()
+        check(lib().cdct_matrix(self._h, which, buf))
+        arr = np.frombuffer(buf, dtype=np.float64).copy()
+        return arr if which == MATRIX_S else arr.reshape(n, n)
+
+    def block_count(self, img) -> int:
+        d = image_desc(img)
+        out = ctypes.c_int64()
+        check(lib().cdct_block_count(self._h, ctypes.byref(d), ctypes.byref(out)))
+        return out.value
+
+    def workspace_size(self, img) -> int:
+        d = image_desc(img)
+        out = ctypes.c_size_t()
+        check(lib().cdct_workspace_size(self._h, ctypes.byref(d), ctypes.byref(out)))
+        return out.value
+
+    def workspace(self, img):
+        torch = _torch()
+        nbytes = self.workspace_size(img)
+        return torch.empty(max(1, nbytes // 8), dtype=torch.float64, device=img.device)
+
+    # -- pipeline calls --------------------------------------------------------
+    def _coeff_dtype(self):
+        torch = _torch()
+        return torch.float32 if self.variant == "exact" else torch.int32
+
+    def forward(self, img, stream=None):
+        """Block-major coefficients [B, nby, nbx, N, N] (int32; float32 for exact)."""
+        torch = _torch()
+        d = image_desc(img)
+        n = self.n
+        nby, nbx = -(-d.height // n), -(-d.width // n)
+        coeff = torch.empty((d.batch, nby, nbx, n, n), dtype=self._coeff_dtype(), device=img.device)
+        check(lib().cdct_forward(self._h, ctypes.byref(d), coeff.data_ptr(), stream_handle(stream)))
+        return coeff
+
+    def zonal(self, coeff, r: int, scaled: bool = False, kept: bool = False, stream=None):
+        """Mask coeff in place; optionally return scaled B and the kept coefficients."""
+        torch = _torch()
+        n = self.n
+        nblocks = coeff.numel() // (n * n)
+        sc = torch.empty(coeff.shape, dtype=torch.float32, device=coeff.device) if scaled else None
+        kp = torch.empty((*coeff.shape[:-2], r), dtype=coeff.dtype, device=coeff.device) if kept else None
+        check(lib().cdct_zonal(self._h, r, coeff.data_ptr(), nblocks,
+                               sc.data_ptr() if sc is not None else None,
+                               kp.data_ptr() if kp is not None else None, stream_handle(stream)))
+        return coeff, sc, kp
+
+    def inverse(self, coeff, width: int, height: int, out=None, stream=None):
+        """Reconstruction [B, H, W] float32 from block-major coefficients."""
+        torch = _torch()
+        b = coeff.shape[0]
+        if out is None:
+            out = torch.empty((b, height, width), dtype=torch.float32, device=coeff.device)
+        check(lib().cdct_inverse(self._h, coeff.data_ptr(), width, height, b, out.data_ptr(),
+                                 out.stride(1), out.stride(0) if b > 1 else height * out.stride(1),
+                                 stream_handle(stream)))
+        return out
+
+    def fwd_zonal_inv(self, img, r: int, out=None, kept: bool = False, psnr: bool = True,
+                      workspace=None, psnr_out=None, kept_out=None, stream=None):
+        """Fused forward -> zonal(r) -> inverse (+ per-image PSNR on the device).
+
+        Returns (recon [B, H, W] float32, kept [B, nby, nbx, r] or None,
+        psnr [B] float64 on the device or None).
+        """
+        torch = _torch()
+        d = image_desc(img)
+        n = self.n
+        if out is None:
+            out = torch.empty((d.batch, d.height, d.width), dtype=torch.float32, device=img.device)
+        o3 = out if out.dim() == 3 else out.unsqueeze(0)
+        kp = kept_out
+        if kept and kp is None:
+            nby, nbx = -(-d.height // n), -(-d.width // n)
+            kp = torch.empty((d.batch, nby, nbx, r), dtype=self._coeff_dtype(), device=img.device)
+        ps = psnr_out
+        if psnr and ps is None:
+            ps = torch.empty(d.batch, dtype=torch.float64, device=img.device)
+        ws = workspace
+        if psnr and ws is None:
+            ws = self.workspace(img)
+        check(lib().cdct_fwd_zonal_inv(
+            self._h, ctypes.byref(d), r, o3.data_ptr(), o3.stride(1),
+            o3.stride(0) if d.batch > 1 else d.height * o3.stride(1),
+            kp.data_ptr() if kp is not None else None,
+            ps.data_ptr() if ps is not None else None,
+            ws.data_ptr() if ws is not None else None,
+            ws.numel() * ws.element_size() if ws is not None else 0,
+            stream_handle(stream)))
+        return out, kp, ps
+
+
+_PSNR_PLAN = None
+
+
+def _psnr_plan():
+    # cdct_workspace_size() of any plan covers the standalone PSNR reduction
+    global _PSNR_PLAN
+    if _PSNR_PLAN is None:
+        _PSNR_PLAN = Plan(8, "hat")
+    return _PSNR_PLAN
+
+
+def psnr(ref, recon, workspace=None, stream=None):
+    """Per-image PSNR [B] (float64, device) of a float32 reconstruction against ref."""
+    torch = _torch()
+    d = image_desc(ref)
+    r3 = recon if recon.dim() == 3 else recon.unsqueeze(0)
+    out = torch.empty(d.batch, dtype=torch.float64, device=ref.device)
+    if workspace is None:
+        workspace = _psnr_plan().workspace(ref)
+    check(lib().cdct_psnr(ctypes.byref(d), r3.data_ptr(), r3.stride(1),
+                          r3.stride(0) if d.batch > 1 else d.height * r3.stride(1),
+                          out.data_ptr(), workspace.data_ptr(),
+                          workspace.numel() * workspace.element_size(), stream_handle(stream)))
+    return out

@@ -1,0 +1,339 @@
+// C ABI (include/cdct.h): argument checking, plans and kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/cdct.h"
+#include "butterfly.cuh"
+#include "common.cuh"
+
+using namespace cdct;
+
+struct cdct_plan_s {
+  int n, variant, conv;
+  double T[32 * 32];
+  double U[32 * 32];
+  double S[32];
+  float s_f[32];
+  KernelSet ks[2];  // per input dtype
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+cdct_status fail(cdct_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+cdct_status cuda_fail(int code, const char* where) {
+  return fail(CDCT_ECUDA, std::string(where) + ": " + cudaGetErrorString(static_cast<cudaError_t>(code)));
+}
+
+constexpr int rows_per_thread(int n) { return 64 / n; }
+constexpr int threads_per_block(int n) { return n / rows_per_thread(n); }
+constexpr int blocks_per_cta(int n) { return kThreads / threads_per_block(n); }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Apply one of the library's 1-D operators to every unit vector (host side).
+template <int N, class P>
+void build_int_matrices(double* T, double* U) {
+  for (int j = 0; j < N; ++j) {
+    int x[N], w[N];
+    for (int i = 0; i < N; ++i) x[i] = w[i] = (i == j);
+    Jam<N, P>::T(x);
+    Jam<N, P>::W(w);  // 2 U
+    for (int i = 0; i < N; ++i) {
+      T[i * N + j] = x[i];
+      U[i * N + j] = w[i] / 2;  // W = 2U is even: exact
+    }
+  }
+}
+
+void build_exact_matrices(double* T, double* U) {
+  for (int j = 0; j < 8; ++j) {
+    float x[8], y[8];
+    for (int i = 0; i < 8; ++i) x[i] = y[i] = (i == j) ? 1.f : 0.f;
+    T8_apply<ParamsExact>(x);   // 2 C
+    T8t_apply<ParamsExact>(y);  // 2 C^T
+    for (int i = 0; i < 8; ++i) {
+      T[i * 8 + j] = x[i];
+      U[i * 8 + j] = 2.0 * y[i];  // N T^{-1} = 8 (2C)^{-1} = 4 C^T
+    }
+  }
+}
+
+KernelSet select_kernels(int n, int variant, int conv, int dtype) {
+  if (variant == CDCT_EXACT) return kernels_exact8(dtype);
+  if (n == 8) return kernels_n8(variant, conv, dtype);
+  if (n == 16) return kernels_n16(variant, conv, dtype);
+  return kernels_n32(variant, conv, dtype);
+}
+
+cdct_status check_image(const cdct_image* in, const char* what) {
+  if (in == nullptr) return fail(CDCT_EINVAL, std::string(what) + ": null image descriptor");
+  if (in->data == nullptr) return fail(CDCT_EINVAL, std::string(what) + ": null data pointer");
+  if (in->dtype != CDCT_U8 && in->dtype != CDCT_I16) return fail(CDCT_EINVAL, std::string(what) + ": bad dtype");
+  if (in->width < 1 || in->height < 1) return fail(CDCT_EINVAL, std::string(what) + ": width and height must be >= 1");
+  if (in->pitch < in->width) return fail(CDCT_EINVAL, std::string(what) + ": pitch < width");
+  if (in->batch < 1) return fail(CDCT_EINVAL, std::string(what) + ": batch must be >= 1");
+  if (in->batch > 1 && in->batch_stride < in->pitch * in->height)
+    return fail(CDCT_EINVAL, std::string(what) + ": batch_stride < pitch * height");
+  return CDCT_OK;
+}
+
+cdct_status check_recon(const float* recon, int64_t pitch, int64_t bstride, int width, int height, int batch) {
+  if (recon == nullptr) return fail(CDCT_EINVAL, "null reconstruction pointer");
+  if (pitch < width) return fail(CDCT_EINVAL, "recon_pitch < width");
+  if (batch > 1 && bstride < pitch * height) return fail(CDCT_EINVAL, "recon_batch_stride < recon_pitch * height");
+  return CDCT_OK;
+}
+
+// Geometry shared by the block kernels.
+void fill_geometry(const cdct_plan_s* p, int width, int height, BlockArgs& a) {
+  const int n = p->n;
+  a.width = width;
+  a.height = height;
+  a.nbx = (width + n - 1) / n;
+  a.nby = (height + n - 1) / n;
+  a.blocks_per_img = static_cast<long long>(a.nbx) * a.nby;
+  const int bpc = blocks_per_cta(n);
+  a.ctas_per_img = static_cast<int>((a.blocks_per_img + bpc - 1) / bpc);
+}
+
+void fill_mask(const cdct_plan_s* p, int r, BlockArgs& a) {
+  const int n = p->n, w = rows_per_thread(n), np = threads_per_block(n);
+  for (int s = 0; s < 16; ++s) a.slab_mask[s] = 0ull;
+  for (int s = 0; s < np; ++s)
+    for (int k = 0; k < w; ++k)
+      for (int i = 0; i < n; ++i)
+        if (zigzag_pos(n, i, s * w + k) < r) a.slab_mask[s] |= 1ull << (k * n + i);
+}
+
+void fill_input(const cdct_image* in, BlockArgs& a) {
+  const int es = in->dtype == CDCT_I16 ? 2 : 1;
+  a.in = in->data;
+  a.in_pitch = in->pitch;
+  a.in_bstride = in->batch > 1 ? in->batch_stride : 0;
+  a.in_vec = aligned16(in->data) && (in->pitch * es) % 16 == 0 &&
+             (in->batch == 1 || (in->batch_stride * es) % 16 == 0);
+}
+
+void fill_output(float* recon, int64_t pitch, int64_t bstride, int batch, BlockArgs& a) {
+  a.out = recon;
+  a.out_pitch = pitch;
+  a.out_bstride = batch > 1 ? bstride : 0;
+  a.out_vec = aligned16(recon) && (pitch * 4) % 16 == 0 && (batch == 1 || (bstride * 4) % 16 == 0);
+}
+
+size_t partial_count(const cdct_plan_s* p, int width, int height, int batch) {
+  BlockArgs a;
+  fill_geometry(p, width, height, a);
+  const long long per = std::max<long long>(a.ctas_per_img, psnr_parts_per_img(height));
+  return static_cast<size_t>(per) * batch;
+}
+
+// scale from the integer kernel result to pixels: fused 4Z; inverse-only 2Z (paper) / 4Z
+float recon_scale(const cdct_plan_s* p, bool fused) {
+  if (p->variant == CDCT_EXACT) return fused ? 1.f / 16.f : 1.f / 4.f;
+  const int mult = (fused || p->conv == 1) ? 4 : 2;
+  return 1.f / static_cast<float>(mult * p->n * p->n);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cdct_last_error(void) { return g_err.c_str(); }
+
+const char* cdct_version(void) { return "cdct 0.1.0 (sm_103a)"; }
+
+cdct_status cdct_plan_create(int n, int variant, uint32_t flags, cdct_plan* out) {
+  if (out == nullptr) return fail(CDCT_EINVAL, "null output plan pointer");
+  *out = nullptr;
+  if (n != 8 && n != 16 && n != 32) return fail(CDCT_EINVAL, "n must be 8, 16 or 32");
+  if (variant != CDCT_EXACT && variant != CDCT_TILDE && variant != CDCT_HAT)
+    return fail(CDCT_EINVAL, "unknown variant");
+  if (flags & ~CDCT_CONV_TRANSPOSE) return fail(CDCT_EINVAL, "unknown flag bits");
+  if (variant == CDCT_EXACT && n != 8)
+    return fail(CDCT_EUNSUPPORTED, "the exact DCT variant is provided for n = 8 only");
+  cdct_plan_s* p = new (std::nothrow) cdct_plan_s();
+  if (p == nullptr) return fail(CDCT_ENOMEM, "plan allocation failed");
+  p->n = n;
+  p->variant = variant;
+  p->conv = (flags & CDCT_CONV_TRANSPOSE) ? 1 : 0;
+  if (variant == CDCT_EXACT) build_exact_matrices(p->T, p->U);
+  else if (variant == CDCT_TILDE) {
+    if (n == 8) build_int_matrices<8, ParamsTilde>(p->T, p->U);
+    else if (n == 16) build_int_matrices<16, ParamsTilde>(p->T, p->U);
+    else build_int_matrices<32, ParamsTilde>(p->T, p->U);
+  } else {
+    if (n == 8) build_int_matrices<8, ParamsHat>(p->T, p->U);
+    else if (n == 16) build_int_matrices<16, ParamsHat>(p->T, p->U);
+    else build_int_matrices<32, ParamsHat>(p->T, p->U);
+  }
+  for (int i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int j = 0; j < n; ++j) d += p->T[i * n + j] * p->T[i * n + j];
+    p->S[i] = 1.0 / std::sqrt(d);
+    p->s_f[i] = static_cast<float>(p->S[i]);
+  }
+  p->ks[0] = select_kernels(n, variant, p->conv, 0);
+  p->ks[1] = select_kernels(n, variant, p->conv, 1);
+  *out = p;
+  return CDCT_OK;
+}
+
+cdct_status cdct_plan_destroy(cdct_plan plan) {
+  delete plan;
+  return CDCT_OK;
+}
+
+cdct_status cdct_block_count(cdct_plan plan, const cdct_image* in, int64_t* n_blocks) {
+  if (plan == nullptr || n_blocks == nullptr) return fail(CDCT_EINVAL, "null argument");
+  cdct_status st = check_image(in, "block_count");
+  if (st != CDCT_OK) return st;
+  BlockArgs a;
+  fill_geometry(plan, in->width, in->height, a);
+  *n_blocks = a.blocks_per_img * in->batch;
+  return CDCT_OK;
+}
+
+cdct_status cdct_workspace_size(cdct_plan plan, const cdct_image* in, size_t* bytes) {
+  if (plan == nullptr || bytes == nullptr) return fail(CDCT_EINVAL, "null argument");
+  cdct_status st = check_image(in, "workspace_size");
+  if (st != CDCT_OK) return st;
+  *bytes = partial_count(plan, in->width, in->height, in->batch) * sizeof(double);
+  return CDCT_OK;
+}
+
+cdct_status cdct_forward(cdct_plan plan, const cdct_image* in, void* coeff, void* stream) {
+  if (plan == nullptr) return fail(CDCT_EINVAL, "null plan");
+  cdct_status st = check_image(in, "forward");
+  if (st != CDCT_OK) return st;
+  if (coeff == nullptr || !aligned16(coeff)) return fail(CDCT_EINVAL, "coeff must be a 16-byte aligned device pointer");
+  BlockArgs a;
+  std::memset(&a, 0, sizeof(a));
+  fill_geometry(plan, in->width, in->height, a);
+  fill_input(in, a);
+  a.coeff = coeff;
+  const int rc = plan->ks[in->dtype].forward(a, in->batch, stream);
+  return rc ? cuda_fail(rc, "forward launch") : CDCT_OK;
+}
+
+cdct_status cdct_zonal(cdct_plan plan, int r, void* coeff, int64_t n_blocks, float* scaled, void* kept,
+                       void* stream) {
+  if (plan == nullptr || coeff == nullptr) return fail(CDCT_EINVAL, "null argument");
+  if (r < 1 || r > plan->n * plan->n) return fail(CDCT_EINVAL, "r must be in [1, N*N]");
+  if (n_blocks < 0) return fail(CDCT_EINVAL, "n_blocks < 0");
+  const int rc = launch_zonal(plan->n, plan->variant == CDCT_EXACT, plan->conv, plan->s_f, r, coeff, n_blocks,
+                              scaled, kept, stream);
+  return rc ? cuda_fail(rc, "zonal launch") : CDCT_OK;
+}
+
+cdct_status cdct_inverse(cdct_plan plan, const void* coeff, int32_t width, int32_t height, int32_t batch,
+                         float* recon, int64_t recon_pitch, int64_t recon_batch_stride, void* stream) {
+  if (plan == nullptr) return fail(CDCT_EINVAL, "null plan");
+  if (coeff == nullptr || !aligned16(coeff)) return fail(CDCT_EINVAL, "coeff must be a 16-byte aligned device pointer");
+  if (width < 1 || height < 1 || batch < 1) return fail(CDCT_EINVAL, "width, height and batch must be >= 1");
+  cdct_status st = check_recon(recon, recon_pitch, recon_batch_stride, width, height, batch);
+  if (st != CDCT_OK) return st;
+  BlockArgs a;
+  std::memset(&a, 0, sizeof(a));
+  fill_geometry(plan, width, height, a);
+  a.coeff = const_cast<void*>(coeff);
+  a.in = coeff;  // never dereferenced as pixels by the inverse kernels
+  fill_output(recon, recon_pitch, recon_batch_stride, batch, a);
+  a.scale = recon_scale(plan, false);
+  const int rc = plan->ks[0].inverse(a, batch, stream);
+  return rc ? cuda_fail(rc, "inverse launch") : CDCT_OK;
+}
+
+cdct_status cdct_psnr(const cdct_image* ref, const float* recon, int64_t recon_pitch, int64_t recon_batch_stride,
+                      double* psnr_db, void* workspace, size_t workspace_bytes, void* stream) {
+  cdct_status st = check_image(ref, "psnr");
+  if (st != CDCT_OK) return st;
+  st = check_recon(recon, recon_pitch, recon_batch_stride, ref->width, ref->height, ref->batch);
+  if (st != CDCT_OK) return st;
+  if (psnr_db == nullptr) return fail(CDCT_EINVAL, "null psnr output");
+  const int parts = psnr_parts_per_img(ref->height);
+  const size_t need = static_cast<size_t>(parts) * ref->batch * sizeof(double);
+  if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 7u))
+    return fail(CDCT_EINVAL, "workspace missing, misaligned or smaller than cdct_workspace_size()");
+  double* partial = static_cast<double*>(workspace);
+  int rc = launch_psnr_partials(ref->data, ref->dtype, ref->pitch, ref->batch > 1 ? ref->batch_stride : 0, recon,
+                                recon_pitch, ref->batch > 1 ? recon_batch_stride : 0, ref->width, ref->height,
+                                ref->batch, partial, parts, stream);
+  if (rc) return cuda_fail(rc, "psnr launch");
+  FinalArgs f;
+  f.partial = partial;
+  f.parts_per_img = parts;
+  f.npix = static_cast<long long>(ref->width) * ref->height;
+  f.psnr = psnr_db;
+  f.sse = nullptr;
+  rc = launch_finalize(f, ref->batch, stream);
+  return rc ? cuda_fail(rc, "psnr finalize launch") : CDCT_OK;
+}
+
+cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, float* recon, int64_t recon_pitch,
+                               int64_t recon_batch_stride, void* kept, double* psnr_db, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+  if (plan == nullptr) return fail(CDCT_EINVAL, "null plan");
+  cdct_status st = check_image(in, "fwd_zonal_inv");
+  if (st != CDCT_OK) return st;
+  if (r < 1 || r > plan->n * plan->n) return fail(CDCT_EINVAL, "r must be in [1, N*N]");
+  st = check_recon(recon, recon_pitch, recon_batch_stride, in->width, in->height, in->batch);
+  if (st != CDCT_OK) return st;
+  if (kept != nullptr && (reinterpret_cast<uintptr_t>(kept) & 3u)) return fail(CDCT_EINVAL, "kept must be 4-byte aligned");
+  BlockArgs a;
+  std::memset(&a, 0, sizeof(a));
+  fill_geometry(plan, in->width, in->height, a);
+  fill_input(in, a);
+  fill_output(recon, recon_pitch, recon_batch_stride, in->batch, a);
+  fill_mask(plan, r, a);
+  a.r = r;
+  a.kept = kept;
+  a.scale = recon_scale(plan, true);
+  if (psnr_db != nullptr) {
+    const size_t need = static_cast<size_t>(a.ctas_per_img) * in->batch * sizeof(double);
+    if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 7u))
+      return fail(CDCT_EINVAL, "workspace missing, misaligned or smaller than cdct_workspace_size()");
+    a.partial = static_cast<double*>(workspace);
+  }
+  int rc = plan->ks[in->dtype].fused(a, in->batch, stream);
+  if (rc) return cuda_fail(rc, "fused launch");
+  if (psnr_db != nullptr) {
+    FinalArgs f;
+    f.partial = a.partial;
+    f.parts_per_img = a.ctas_per_img;
+    f.npix = static_cast<long long>(in->width) * in->height;
+    f.psnr = psnr_db;
+    f.sse = nullptr;
+    rc = launch_finalize(f, in->batch, stream);
+    if (rc) return cuda_fail(rc, "psnr finalize launch");
+  }
+  return CDCT_OK;
+}
+
+cdct_status cdct_matrix(cdct_plan plan, int which, double* out) {
+  if (plan == nullptr || out == nullptr) return fail(CDCT_EINVAL, "null argument");
+  const int n = plan->n;
+  switch (which) {
+    case CDCT_MATRIX_T: std::memcpy(out, plan->T, sizeof(double) * n * n); return CDCT_OK;
+    case CDCT_MATRIX_U: std::memcpy(out, plan->U, sizeof(double) * n * n); return CDCT_OK;
+    case CDCT_MATRIX_S: std::memcpy(out, plan->S, sizeof(double) * n); return CDCT_OK;
+    case CDCT_MATRIX_ZIGZAG:
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) out[i * n + j] = zigzag_pos(n, i, j);
+      return CDCT_OK;
+    default: return fail(CDCT_EINVAL, "unknown matrix selector");
+  }
+}
+
+}  // extern "C"
