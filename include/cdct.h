@@ -140,6 +140,13 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
                                double* psnr_db, void* workspace, size_t workspace_bytes,
                                void* stream);
 
+/* Synchronise `stream` and report whether a kernel of this library gave up
+ * a bounded wait on the current device since the last check (the fused
+ * kernel waits, with a time limit of about one second, for the bulk copies
+ * that stage its input).  Returns CDCT_ETIMEOUT and clears the record if so,
+ * CDCT_OK otherwise.  Outputs of a call that timed out are incomplete. */
+cdct_status cdct_check_device(void* stream);
+
 /* Host copy of a plan matrix (CDCT_MATRIX_*), computed by running the
  * library's own butterflies on unit vectors.  `out` is host memory of N*N
  * doubles (N for CDCT_MATRIX_S). */

@@ -23,7 +23,7 @@ MATRIX_T, MATRIX_U, MATRIX_S, MATRIX_ZIGZAG = range(4)
 EXPORTS = (
     "cdct_plan_create", "cdct_plan_destroy", "cdct_block_count", "cdct_workspace_size",
     "cdct_forward", "cdct_zonal", "cdct_inverse", "cdct_psnr", "cdct_fwd_zonal_inv",
-    "cdct_matrix", "cdct_last_error", "cdct_version",
+    "cdct_matrix", "cdct_last_error", "cdct_version", "cdct_check_device",
 )
 
 
@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cdct_matrix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "cdct_last_error": (ctypes.c_char_p, []),
         "cdct_version": (ctypes.c_char_p, []),
+        "cdct_check_device": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -80,6 +81,11 @@ def lib() -> ctypes.CDLL:
     if _LIB is None:
         _LIB = load_library()
     return _LIB
+
+
+def check_device(stream=None) -> None:
+    """Synchronise the stream; raise if a kernel gave up a bounded wait."""
+    check(lib().cdct_check_device(stream_handle(stream)))
 
 
 def check(status: int) -> None:

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -12,6 +13,10 @@
 #include "common.cuh"
 
 using namespace cdct;
+
+// Device word the kernels set when a bounded wait gives up (see
+// cdct_check_device); one per device, reached through its symbol address.
+static __device__ int g_device_error;
 
 struct cdct_plan_s {
   int n, variant, conv;
@@ -40,6 +45,41 @@ constexpr int threads_per_block(int n) { return n / rows_per_thread(n); }
 constexpr int blocks_per_cta(int n) { return kThreads / threads_per_block(n); }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+constexpr int kMaxDevices = 64;
+
+// per-device cache of the SM count and of the error word's address
+struct DeviceInfo {
+  int sms = 0;
+  int* err = nullptr;
+};
+DeviceInfo g_dev[kMaxDevices];
+
+int device_info(DeviceInfo** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  if (dev < 0 || dev >= kMaxDevices) return static_cast<int>(cudaErrorInvalidDevice);
+  DeviceInfo& d = g_dev[dev];
+  if (d.err == nullptr) {
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_device_error);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    d.sms = sms;
+    d.err = static_cast<int*>(p);
+  }
+  *out = &d;
+  return 0;
+}
+
+int pipe_launch(int n, int variant, int conv, int dtype, const PipeArgs& pa, int r, int sms, void* stream) {
+  if (n == 8) return pipe_launch_n8(variant, conv, dtype, pa, r, sms, stream);
+  if (n == 16) return pipe_launch_n16(variant, conv, dtype, pa, r, sms, stream);
+  return pipe_launch_n32(variant, conv, dtype, pa, r, sms, stream);
+}
 
 // Apply one of the library's 1-D operators to every unit vector (host side).
 template <int N, class P>
@@ -132,10 +172,17 @@ void fill_output(float* recon, int64_t pitch, int64_t bstride, int batch, BlockA
   a.out_vec = aligned16(recon) && (pitch * 4) % 16 == 0 && (batch == 1 || (bstride * 4) % 16 == 0);
 }
 
+// pipelined-kernel work units: segments of up to blocks_per_cta(n) blocks
+long long units_per_row(const cdct_plan_s* p, const BlockArgs& a) {
+  const int s = blocks_per_cta(p->n);
+  return (a.nbx + s - 1) / s;
+}
+
 size_t partial_count(const cdct_plan_s* p, int width, int height, int batch) {
   BlockArgs a;
   fill_geometry(p, width, height, a);
-  const long long per = std::max<long long>(a.ctas_per_img, psnr_parts_per_img(height));
+  long long per = std::max<long long>(a.ctas_per_img, psnr_parts_per_img(height));
+  per = std::max<long long>(per, units_per_row(p, a) * a.nby);
   return static_cast<size_t>(per) * batch;
 }
 
@@ -300,18 +347,40 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
   a.r = r;
   a.kept = kept;
   a.scale = recon_scale(plan, true);
+  const int es = in->dtype == CDCT_I16 ? 2 : 1;
+  const bool pipe = plan->variant != CDCT_EXACT && a.in_vec && (static_cast<long long>(in->width) * es) % 16 == 0;
+  PipeArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  long long parts_per_img = a.ctas_per_img;
+  if (pipe) {
+    pa.units_per_row = static_cast<int>(units_per_row(plan, a));
+    pa.units_per_img = static_cast<long long>(pa.units_per_row) * a.nby;
+    pa.total_units = pa.units_per_img * in->batch;
+    pa.wait_limit = 1ll << 31;   // about one second of SM clock
+    parts_per_img = pa.units_per_img;
+  }
   if (psnr_db != nullptr) {
-    const size_t need = static_cast<size_t>(a.ctas_per_img) * in->batch * sizeof(double);
+    const size_t need = static_cast<size_t>(parts_per_img) * in->batch * sizeof(double);
     if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 7u))
       return fail(CDCT_EINVAL, "workspace missing, misaligned or smaller than cdct_workspace_size()");
     a.partial = static_cast<double*>(workspace);
   }
-  int rc = plan->ks[in->dtype].fused(a, in->batch, stream);
+  int rc;
+  if (pipe) {
+    DeviceInfo* di = nullptr;
+    rc = device_info(&di);
+    if (rc) return cuda_fail(rc, "device query");
+    pa.b = a;
+    pa.err = di->err;
+    rc = pipe_launch(plan->n, plan->variant, plan->conv, in->dtype, pa, r, di->sms, stream);
+  } else {
+    rc = plan->ks[in->dtype].fused(a, in->batch, stream);
+  }
   if (rc) return cuda_fail(rc, "fused launch");
   if (psnr_db != nullptr) {
     FinalArgs f;
     f.partial = a.partial;
-    f.parts_per_img = a.ctas_per_img;
+    f.parts_per_img = static_cast<int>(parts_per_img);
     f.npix = static_cast<long long>(in->width) * in->height;
     f.psnr = psnr_db;
     f.sse = nullptr;
@@ -319,6 +388,22 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
     if (rc) return cuda_fail(rc, "psnr finalize launch");
   }
   return CDCT_OK;
+}
+
+cdct_status cdct_check_device(void* stream) {
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  rc = static_cast<int>(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  if (rc) return cuda_fail(rc, "stream synchronize");
+  int word = 0;
+  rc = static_cast<int>(cudaMemcpy(&word, di->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (rc) return cuda_fail(rc, "error word read");
+  if (word == 0) return CDCT_OK;
+  const int zero = 0;
+  rc = static_cast<int>(cudaMemcpy(di->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  if (rc) return cuda_fail(rc, "error word reset");
+  return fail(CDCT_ETIMEOUT, "a kernel gave up waiting for its staged input (bounded wait expired)");
 }
 
 cdct_status cdct_matrix(cdct_plan plan, int which, double* out) {

@@ -55,6 +55,20 @@ KernelSet kernels_n16(int variant, int conv, int dtype);
 KernelSet kernels_n32(int variant, int conv, int dtype);
 KernelSet kernels_exact8(int dtype);
 
+// Launch arguments of the persistent pipelined fused kernel.
+struct PipeArgs {
+  BlockArgs b;
+  int units_per_row;       // segments of up to 128/P blocks per block row
+  long long units_per_img;
+  long long total_units;
+  int* err;                // device error word (bit 0: a bulk copy never landed)
+  long long wait_limit;    // SM cycles before a stage wait gives up
+};
+
+int pipe_launch_n8(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream);
+int pipe_launch_n16(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream);
+int pipe_launch_n32(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream);
+
 int launch_finalize(const FinalArgs& a, int batch, void* stream);
 int launch_zonal(int n, int exact, int conv, const float* s, int r, void* coeff, long long nblocks,
                  float* scaled, void* kept, void* stream);
@@ -66,7 +80,7 @@ int psnr_parts_per_img(int height);
 
 // Zig-zag position of (i, j) in an n x n block (anti-diagonals in order;
 // row index falling on even diagonals, rising on odd ones).
-__host__ __device__ __forceinline__ int zigzag_pos(int n, int i, int j) {
+__host__ __device__ constexpr int zigzag_pos(int n, int i, int j) {
   const int d = i + j;
   if (d < n) {
     const int start = d * (d + 1) / 2;

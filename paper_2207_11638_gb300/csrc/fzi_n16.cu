@@ -1,5 +1,6 @@
 // Instantiations of the integer block kernels for N = 16.
 #include "block_kernels.cuh"
+#include "pipe_kernels.cuh"
 
 namespace cdct {
 
@@ -8,6 +9,24 @@ KernelSet kernels_n16(int variant, int conv, int dtype) {
     return conv == 0 ? kernel_set_int<16, ParamsTilde, 0>(dtype) : kernel_set_int<16, ParamsTilde, 1>(dtype);
   }
   return conv == 0 ? kernel_set_int<16, ParamsHat, 0>(dtype) : kernel_set_int<16, ParamsHat, 1>(dtype);
+}
+
+// Pipelined fused kernel: compile-time r for the paper convention at
+// r in {64}; any other r (and the transpose convention) uses the
+// runtime mask.
+template <class P, typename InT>
+static int pipe_n16(int conv, const PipeArgs& pa, int r, int num_sms, void* stream) {
+  if (conv == 0) return pipe_launch_r<16, P, 0, InT, 2, 64>(pa, r, num_sms, stream);
+  return pipe_launch_r<16, P, 1, InT, 2>(pa, r, num_sms, stream);
+}
+
+int pipe_launch_n16(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream) {
+  if (variant == 1) {
+    return dtype == 0 ? pipe_n16<ParamsTilde, uint8_t>(conv, pa, r, num_sms, stream)
+                      : pipe_n16<ParamsTilde, int16_t>(conv, pa, r, num_sms, stream);
+  }
+  return dtype == 0 ? pipe_n16<ParamsHat, uint8_t>(conv, pa, r, num_sms, stream)
+                    : pipe_n16<ParamsHat, int16_t>(conv, pa, r, num_sms, stream);
 }
 
 }  // namespace cdct

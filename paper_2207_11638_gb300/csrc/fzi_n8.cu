@@ -1,5 +1,6 @@
 // Instantiations of the integer block kernels for N = 8.
 #include "block_kernels.cuh"
+#include "pipe_kernels.cuh"
 
 namespace cdct {
 
@@ -8,6 +9,24 @@ KernelSet kernels_n8(int variant, int conv, int dtype) {
     return conv == 0 ? kernel_set_int<8, ParamsTilde, 0>(dtype) : kernel_set_int<8, ParamsTilde, 1>(dtype);
   }
   return conv == 0 ? kernel_set_int<8, ParamsHat, 0>(dtype) : kernel_set_int<8, ParamsHat, 1>(dtype);
+}
+
+// Pipelined fused kernel: compile-time r for the paper convention at
+// r in {1, 6, 10, 16, 28, 64}; any other r (and the transpose convention) uses the
+// runtime mask.
+template <class P, typename InT>
+static int pipe_n8(int conv, const PipeArgs& pa, int r, int num_sms, void* stream) {
+  if (conv == 0) return pipe_launch_r<8, P, 0, InT, 3, 1, 6, 10, 16, 28, 64>(pa, r, num_sms, stream);
+  return pipe_launch_r<8, P, 1, InT, 3>(pa, r, num_sms, stream);
+}
+
+int pipe_launch_n8(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream) {
+  if (variant == 1) {
+    return dtype == 0 ? pipe_n8<ParamsTilde, uint8_t>(conv, pa, r, num_sms, stream)
+                      : pipe_n8<ParamsTilde, int16_t>(conv, pa, r, num_sms, stream);
+  }
+  return dtype == 0 ? pipe_n8<ParamsHat, uint8_t>(conv, pa, r, num_sms, stream)
+                    : pipe_n8<ParamsHat, int16_t>(conv, pa, r, num_sms, stream);
 }
 
 }  // namespace cdct
