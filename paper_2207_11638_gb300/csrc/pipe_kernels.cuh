@@ -31,13 +31,18 @@
 
 namespace cdct {
 
-// zig-zag cut: highest row / column index + 1 among the first r positions
+// zig-zag cut: 1 + the highest row or column index among the first r
+// positions (rows and columns can differ by one: an even partial diagonal
+// starts at its bottom-left end, an odd one at its top-right end)
 __host__ __device__ constexpr int zonal_extent(int n, int r) {
-  int jc = 0;
+  int e = 0;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
-      if (zigzag_pos(n, i, j) < r && j + 1 > jc) jc = j + 1;
-  return jc;
+      if (zigzag_pos(n, i, j) < r) {
+        if (j + 1 > e) e = j + 1;
+        if (i + 1 > e) e = i + 1;
+      }
+  return e;
 }
 
 __host__ __device__ constexpr unsigned long long slab_mask_ct(int n, int r, int p) {
@@ -76,48 +81,51 @@ struct PipeGeo {
   }
 };
 
-// Read W rows of N pixels of block lb from a staged unit.  `valid` = number
-// of valid pixels of this block's rows (N unless the block crosses the right
-// image edge, where columns are clamped to the last valid one).
+// Read row r (N pixels) of block lb from a staged unit with 128-bit shared
+// loads.  `valid` = number of valid pixels of this block's rows (N unless
+// the block crosses the right image edge, where columns are clamped to the
+// last valid one).
+template <int N, typename InT>
+__device__ __forceinline__ void stage_read_row(const unsigned char* stage, int lb, int r, int valid, int (&x)[N]) {
+  typedef PipeGeo<N, InT> PG;
+  const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
+  if (valid < N) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = static_cast<int>(row[min(j, valid - 1)]);
+    return;
+  }
+  if constexpr (sizeof(InT) == 2) {
+#pragma unroll
+    for (int c = 0; c < N / 8; ++c) {      // 16-byte chunks of the block row
+      const uint4 q = lds_v4(row + 8 * c);
+      x[8 * c + 0] = sext_lo16(q.x); x[8 * c + 1] = sext_hi16(q.x);
+      x[8 * c + 2] = sext_lo16(q.y); x[8 * c + 3] = sext_hi16(q.y);
+      x[8 * c + 4] = sext_lo16(q.z); x[8 * c + 5] = sext_hi16(q.z);
+      x[8 * c + 6] = sext_lo16(q.w); x[8 * c + 7] = sext_hi16(q.w);
+    }
+  } else if constexpr (N == 8) {
+    const uint2 q = *reinterpret_cast<const uint2*>(row);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) { x[t] = byte_u8(q.x, t); x[4 + t] = byte_u8(q.y, t); }
+  } else {
+#pragma unroll
+    for (int c = 0; c < N / 16; ++c) {
+      const uint4 q = lds_v4(row + 16 * c);
+      const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[16 * c + 4 * e + t] = byte_u8(wd[e], t);
+    }
+  }
+}
+
+// The W rows of this thread's slab of block lb.
 template <int N, typename InT>
 __device__ __forceinline__ void stage_read_rows(const unsigned char* stage, int lb, int p, int valid,
                                                 int (&v)[Geo<N>::W][N]) {
-  typedef PipeGeo<N, InT> PG;
-  constexpr int W = Geo<N>::W;
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    const int r = p * W + k;
-    const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
-    if (valid < N) {
-#pragma unroll
-      for (int j = 0; j < N; ++j) v[k][j] = static_cast<int>(row[min(j, valid - 1)]);
-      continue;
-    }
-    if constexpr (sizeof(InT) == 2) {
-#pragma unroll
-      for (int c = 0; c < N / 8; ++c) {      // 16-byte chunks of the block row
-        const uint4 q = lds_v4(row + 8 * c);
-        v[k][8 * c + 0] = sext_lo16(q.x); v[k][8 * c + 1] = sext_hi16(q.x);
-        v[k][8 * c + 2] = sext_lo16(q.y); v[k][8 * c + 3] = sext_hi16(q.y);
-        v[k][8 * c + 4] = sext_lo16(q.z); v[k][8 * c + 5] = sext_hi16(q.z);
-        v[k][8 * c + 6] = sext_lo16(q.w); v[k][8 * c + 7] = sext_hi16(q.w);
-      }
-    } else if constexpr (N == 8) {
-      const uint2 q = *reinterpret_cast<const uint2*>(row);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) { v[k][t] = byte_u8(q.x, t); v[k][4 + t] = byte_u8(q.y, t); }
-    } else {
-#pragma unroll
-      for (int c = 0; c < N / 16; ++c) {
-        const uint4 q = lds_v4(row + 16 * c);
-        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-          for (int t = 0; t < 4; ++t) v[k][16 * c + 4 * e + t] = byte_u8(wd[e], t);
-      }
-    }
-  }
+  for (int k = 0; k < Geo<N>::W; ++k) stage_read_row<N, InT>(stage, lb, p * Geo<N>::W + k, valid, v[k]);
 }
 
 // Slab transposes for the pipe kernels (tile per block at lb * TILE_STRIDE).
@@ -196,13 +204,17 @@ __device__ __forceinline__ void pipe_cols_to_rows(int* tiles, int lb, int p, int
   }
 }
 
+// resident CTAs per SM the register allocation is sized for
+template <int N>
+struct PipeOcc { static constexpr int value = (N == 8) ? 4 : 3; };
+
 template <int N, class P, int CONV, typename InT, int RFIX, int STAGES>
-__global__ void __launch_bounds__(kThreads) fzi_pipe_kernel(const PipeArgs pa) {
+__global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(const PipeArgs pa) {
   typedef Geo<N> G;
   typedef PipeGeo<N, InT> PG;
   typedef Ops<N, P, CONV> O;
   constexpr int W = G::W;
-  // columns (and rows) that can hold kept coefficients
+  // rows and columns that can hold kept coefficients
   constexpr int JC = RFIX > 0 ? zonal_extent(N, RFIX) : N;
   const BlockArgs& a = pa.b;
 
@@ -346,11 +358,12 @@ __global__ void __launch_bounds__(kThreads) fzi_pipe_kernel(const PipeArgs pa) {
           if (j < valid) orow[j] = rec[j];
       }
       if (a.partial != nullptr) {
-        const InT* row = reinterpret_cast<const InT*>(stage + (p * W + k) * PG::ROWP) + lb * N;
+        int ref[1][N];
+        stage_read_row<N, InT>(stage, lb, p * W + k, valid, ref[0]);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           if (j < valid) {
-            const float e = rec[j] - static_cast<float>(row[j]);
+            const float e = rec[j] - static_cast<float>(ref[0][j]);
             acc = fmaf(e, e, acc);
           }
         }

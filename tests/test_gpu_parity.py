@@ -204,3 +204,28 @@ def test_still_image_workload_all_r():
         torch.cuda.synchronize()
         assert np.abs(rec.cpu().numpy()[0] - ref["recon"]).max() <= RECON_TOL
         check_psnr(ps.cpu().tolist(), [pl.psnr_float(img, ref["recon"])])
+
+
+# Shapes that take the pipelined (bulk-copy staged) fused kernel: 16-byte
+# aligned rows (width a multiple of 16 bytes), with ragged block tails in
+# both directions, rows longer than one work unit, and several images.
+PIPE_SHAPES = {"u8": ((40, 1056), (77, 48), (5, 16), (130, 2064)),
+               "i16": ((40, 1048), (77, 40), (5, 8), (99, 520))}
+
+
+@pytest.mark.parametrize("n,variant,conv", CASES)
+@pytest.mark.parametrize("dtype", ("u8", "i16"))
+def test_pipelined_path_matches_oracle(n, variant, conv, dtype):
+    plan = b.Plan(n, variant, conv)
+    for si, (h, w) in enumerate(PIPE_SHAPES[dtype]):
+        img = rand_batch(dtype, 2, h, w, seed=1000 + si * 17 + n)
+        dev = to_dev(img)
+        rs = (1, 6, n * n // 4, n * n) if n == 8 else (n * n // 4, 3, n * n)
+        for r in rs:
+            ref = pl.fzi_integer(img, n, variant, r, conv)
+            rec, kept, ps = plan.fwd_zonal_inv(dev, r, kept=True, psnr=True)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(rec.cpu().numpy(), ref["recon"].astype(np.float32))
+            np.testing.assert_array_equal(kept.cpu().numpy(), pl.kept_coeffs(ref["ym"], n, r))
+            check_psnr(ps.cpu().tolist(), oracle_psnr(img, ref["z"], n))
+    b.check_device()
