@@ -199,6 +199,7 @@ def workload_config(args):
 def run_ours(args):
     import torch
     import torch.distributed as dist
+    from paper_2207_11638_gb300 import dist as pdist
     from paper_2207_11638_gb300 import workload as wl
 
     rank, world, local = dist_env()
@@ -207,7 +208,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    luma_h, chroma_h = wl.host_batch(frames=args.frames, seed=2 + 1000 * rank)
+    luma_h, chroma_h = wl.host_batch(frames=args.frames, seed=pdist.rank_seed(2, rank))
     luma_p = torch.from_numpy(luma_h).pin_memory()
     chroma_p = torch.from_numpy(chroma_h).pin_memory()
     luma = luma_p.to(dev)
@@ -221,11 +222,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return pdist.max_over_ranks(x, device=dev)
 
     # ---- device-resident timing -------------------------------------------------
     for _ in range(args.warmup):
@@ -245,7 +242,7 @@ def run_ours(args):
         barrier()
     ms = max_over_ranks(t_start.elapsed_time(t_end))
     clock = clocks.summary()
-    value = px_step * args.steps * world / (ms / 1e3) / 1e9
+    value = pdist.job_throughput(px_step, args.steps, world, ms)
 
     # dominant kernel: the fused call.  Each event pair brackets one pass: the
     # fused launch over the luma planes and over the chroma planes, each with
@@ -285,7 +282,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_ms = max_over_ranks(e_start.elapsed_time(e_end))
-    e2e_value = px_step * e2e_steps * world / (e2e_ms / 1e3) / 1e9
+    e2e_value = pdist.job_throughput(px_step, e2e_steps, world, e2e_ms)
     ps = psnr_host.numpy()
     assert np.all(np.isfinite(ps)) and ps.min() > 0, "PSNR check failed"
 
