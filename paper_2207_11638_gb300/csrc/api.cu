@@ -182,7 +182,7 @@ size_t partial_count(const cdct_plan_s* p, int width, int height, int batch) {
   BlockArgs a;
   fill_geometry(p, width, height, a);
   long long per = std::max<long long>(a.ctas_per_img, psnr_parts_per_img(height));
-  per = std::max<long long>(per, units_per_row(p, a) * a.nby);
+  per = std::max<long long>(per, units_per_row(p, a) * a.nby * (kThreads / 32));
   return static_cast<size_t>(per) * batch;
 }
 
@@ -348,7 +348,8 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
   a.kept = kept;
   a.scale = recon_scale(plan, true);
   const int es = in->dtype == CDCT_I16 ? 2 : 1;
-  const bool pipe = plan->variant != CDCT_EXACT && a.in_vec && (static_cast<long long>(in->width) * es) % 16 == 0;
+  const bool pipe = plan->variant != CDCT_EXACT && a.in_vec && (static_cast<long long>(in->width) * es) % 16 == 0 &&
+                    units_per_row(plan, a) * a.nby * in->batch * (kThreads / 32) < (1ll << 31);
   PipeArgs pa;
   std::memset(&pa, 0, sizeof(pa));
   long long parts_per_img = a.ctas_per_img;
@@ -357,7 +358,12 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
     pa.units_per_img = static_cast<long long>(pa.units_per_row) * a.nby;
     pa.total_units = pa.units_per_img * in->batch;
     pa.wait_limit = 1ll << 31;   // about one second of SM clock
-    parts_per_img = pa.units_per_img;
+    pa.div_img = make_fastdiv(static_cast<uint32_t>(pa.units_per_img));
+    pa.div_row = make_fastdiv(static_cast<uint32_t>(pa.units_per_row));
+    parts_per_img = pa.units_per_img * (kThreads / 32);   // one partial per warp and unit
+    // the pipelined kernel masks 8 x 8 sub-blocks of the folded block
+    const int nsub = (plan->n / 8) * (plan->n / 8);
+    for (int q = 0; q < 16; ++q) a.slab_mask[q] = q < nsub ? sub_mask(plan->n, r, q) : 0ull;
   }
   if (psnr_db != nullptr) {
     const size_t need = static_cast<size_t>(parts_per_img) * in->batch * sizeof(double);

@@ -55,12 +55,24 @@ KernelSet kernels_n16(int variant, int conv, int dtype);
 KernelSet kernels_n32(int variant, int conv, int dtype);
 KernelSet kernels_exact8(int dtype);
 
+// Divisor with its reciprocal for division by multiply-high (see fdiv).
+struct FastDiv {
+  uint32_t d, m;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.m = static_cast<uint32_t>(0xFFFFFFFFull / d);
+  return f;
+}
+
 // Launch arguments of the persistent pipelined fused kernel.
 struct PipeArgs {
   BlockArgs b;
   int units_per_row;       // segments of up to 128/P blocks per block row
   long long units_per_img;
-  long long total_units;
+  long long total_units;   // < 2^31
+  FastDiv div_img, div_row;
   int* err;                // device error word (bit 0: a bulk copy never landed)
   long long wait_limit;    // SM cycles before a stage wait gives up
 };
@@ -89,6 +101,39 @@ __host__ __device__ constexpr int zigzag_pos(int n, int i, int j) {
   const int m = 2 * n - 1 - d;                 // length of diagonal d
   const int start = n * n - m * (m + 1) / 2;
   return start + ((d & 1) ? i - (d - n + 1) : (n - 1) - i);
+}
+
+// zig-zag cut: 1 + the highest row or column index among the first r
+// positions (rows and columns can differ by one: an even partial diagonal
+// starts at its bottom-left end, an odd one at its top-right end)
+__host__ __device__ constexpr int zonal_extent(int n, int r) {
+  int e = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (zigzag_pos(n, i, j) < r) {
+        if (j + 1 > e) e = j + 1;
+        if (i + 1 > e) e = i + 1;
+      }
+  return e;
+}
+
+// Global coefficient row / column of local (i, k) in 8 x 8 sub-block q.
+//   N = 16: q = a*2 + b, row = 2i + a, col = 2k + b
+//   N = 32: q = hr*8 + ar*4 + c with c = h*2 + a',
+//           row = 4i + 2ar + hr, col = 4k + 2a' + h
+__host__ __device__ constexpr int sub_row_of(int n, int q, int i) {
+  return n == 8 ? i : (n == 16 ? 2 * i + (q >> 1) : 4 * i + 2 * ((q >> 2) & 1) + (q >> 3));
+}
+__host__ __device__ constexpr int sub_col_of(int n, int q, int k) {
+  return n == 8 ? k : (n == 16 ? 2 * k + (q & 1) : 4 * k + 2 * (q & 1) + ((q >> 1) & 1));
+}
+// bit (k * 8 + i): keep local row i of local column k of sub-block q
+__host__ __device__ constexpr unsigned long long sub_mask(int n, int r, int q) {
+  unsigned long long m = 0;
+  for (int k = 0; k < 8; ++k)
+    for (int i = 0; i < 8; ++i)
+      if (zigzag_pos(n, sub_row_of(n, q, i), sub_col_of(n, q, k)) < r) m |= 1ull << (k * 8 + i);
+  return m;
 }
 
 }  // namespace cdct

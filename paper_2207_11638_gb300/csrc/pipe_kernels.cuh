@@ -1,27 +1,41 @@
 // Persistent, bulk-copy pipelined fused kernel (forward -> zonal -> inverse
-// -> squared error) for the integer variants.
+// -> squared error) for the integer variants, N = 8, 16, 32.
 //
-// Work unit.  One segment of up to S = 128 / P consecutive blocks of one
-// block row of one image: N pixel rows x (S * N) pixels, 8192 pixels when
-// full.  The grid is persistent (a few CTAs per SM); CTA c takes units
-// c, c + G, c + 2G, ... so every unit and its error partial are fixed.
+// Work unit.  One segment of up to S consecutive blocks of one block row of
+// one image, 8192 pixels when full (S = 128, 32, 8 for N = 8, 16, 32).  The
+// grid is persistent; CTA c takes units c, c + G, c + 2G, ...
 //
 // Pipeline.  The input rows of a unit are staged in shared memory by bulk
-// asynchronous copies (cp.async.bulk, one per pixel row, issued by warp 0)
-// into a STAGES-deep ring; an mbarrier per stage counts the landed bytes.
-// While the CTA computes unit k, the copies for units k+1 .. k+STAGES-1 are
-// in flight, so the HBM read stream never waits for the arithmetic.  Rows
-// past the image bottom are fetched from the last row (edge replication);
-// columns past the right edge are clamped when read from shared memory.
-// The reconstruction goes straight from registers to HBM with 128-bit
-// streaming stores; the squared error against the staged input is summed in
-// float per thread and warp, and one double per unit is written.
+// asynchronous copies (cp.async.bulk, one per pixel row, issued by one warp)
+// into a STAGES-deep ring.  A "full" mbarrier per stage counts the landed
+// bytes.  Every warp owns whole blocks, so a unit needs no CTA-wide barrier:
+// a warp that finishes its part of a unit bumps the stage's counter in
+// shared memory, and the last of the four refills the stage with the next
+// unit.  No warp ever waits for another warp, only for its data.  All waits
+// are bounded (clock64).
 //
-// Zonal pruning.  With a compile-time r (RFIX > 0) only the JC x JC corner
-// that contains the kept zig-zag positions is computed: the forward passes
-// never produce the other outputs and the inverse passes see them as
-// constant zeros, so the butterflies shrink to the adds that matter.  For
-// N = 8 the whole mask is a compile-time constant.
+// Arithmetic.  The 2-D transform of an N x N block factors through the JAM
+// recursion (Sec. 6, Eq. app_N) as
+//     Y = P_N [T_8 G_ab R_8]_ab P_N^T,   G = F_N A F_N^T,
+// where F_N is the cascade of M^add stages (the "fold": M^add_N, then
+// M^add_{N/2} on each half), P_N the even/odd interleaves of M^per, G_ab the
+// (N/8)^2 sub-blocks of size 8 x 8 of the folded block and R_8 the 8-point
+// right factor (2U_8 or T_8^T).  The inverse is the mirror image: sub-block
+// inverses, then the unfold F_N^T ( . ) F_N.  So N = 16 and 32 run the same
+// register 8 x 8 core as N = 8, bracketed by fold / unfold adds that are
+// exactly the M^add stages of the N-point butterflies:
+//   N = 8:  one thread owns one block.
+//   N = 16: a thread owns rows {p, 7-p, 8+p, 15-p} (p < 4) of a block; all
+//           folds are thread-local; a warp-local exchange through shared
+//           memory hands each of the 4 sub-blocks to one thread.
+//   N = 32: a thread owns rows {p, 31-p} (p < 16); the horizontal folds and
+//           the first vertical fold are thread-local; the second vertical
+//           fold (and unfold) is done while reading the exchange buffer.
+// The exchange buffers are XOR-swizzled so that every 128-bit access is
+// bank-conflict free.
+//
+// Error.  The squared error against the staged input is summed per thread in
+// float, reduced per warp, and one double per warp and unit is written.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -31,55 +45,28 @@
 
 namespace cdct {
 
-// zig-zag cut: 1 + the highest row or column index among the first r
-// positions (rows and columns can differ by one: an even partial diagonal
-// starts at its bottom-left end, an odd one at its top-right end)
-__host__ __device__ constexpr int zonal_extent(int n, int r) {
-  int e = 0;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j)
-      if (zigzag_pos(n, i, j) < r) {
-        if (j + 1 > e) e = j + 1;
-        if (i + 1 > e) e = i + 1;
-      }
-  return e;
-}
-
-__host__ __device__ constexpr unsigned long long slab_mask_ct(int n, int r, int p) {
-  unsigned long long m = 0;
-  const int w = 64 / n;
-  for (int k = 0; k < w; ++k)
-    for (int i = 0; i < n; ++i)
-      if (zigzag_pos(n, i, p * w + k) < r) m |= 1ull << (k * n + i);
-  return m;
-}
-
 template <int N, typename InT>
 struct PipeGeo {
-  typedef Geo<N> G;
-  static constexpr int S = G::BPC;                       // blocks per unit
-  static constexpr int WPX = S * N;                      // pixels per unit row
+  static constexpr int P = N == 8 ? 1 : (N == 16 ? 4 : 16);   // threads per block
+  static constexpr int S = kThreads / P;                       // blocks per unit
+  static constexpr int WPX = S * N;                            // pixels per unit row
   static constexpr int ROWB = WPX * static_cast<int>(sizeof(InT));
-  // staged row pitch; N = 32 rows are offset by 16 bytes so that the eight
-  // rows read by one quarter warp fall in different bank groups
+  // staged row pitch; N = 32 rows are offset by 16 bytes so that the rows
+  // p = 0..7 read by one quarter warp fall in different bank groups
   static constexpr int ROWP = ROWB + (N == 32 ? 16 : 0);
   static constexpr int STAGE_BYTES = N * ROWP;
-  static constexpr int TILE_STRIDE = (N == 16) ? N * N + 4 : N * N;  // words
-  static constexpr int TILE_WORDS = (G::P > 1) ? S * TILE_STRIDE : 0;
-  // lane -> (block in unit, slab) mapping
-  static __device__ __forceinline__ void lane_map(int tid, int& lb, int& p) {
-    if constexpr (N == 8) { lb = tid; p = 0; }
-    else if constexpr (N == 16) {       // 8 blocks x 4 slabs per warp, slab-major
-      const int w = tid >> 5, l = tid & 31;
-      p = l >> 3; lb = w * 8 + (l & 7);
-    } else {                            // 2 blocks x 16 slabs per warp, block-major
-      lb = tid / 16; p = tid % 16;
-    }
-  }
+  // exchange buffer (int32 words) per warp: N = 16: 8 blocks of 65 chunks;
+  // N = 32: 2 blocks of 288 chunks (16-byte chunks, padded, see UnitBody)
+  static constexpr int XCH_WARP_WORDS = (N == 8) ? 0 : (N == 16 ? 8 * 65 * 4 : 2 * 288 * 4);
+  static constexpr int XCH_WORDS = XCH_WARP_WORDS * (kThreads / 32);
   static constexpr size_t smem_bytes(int stages) {
-    return static_cast<size_t>(stages) * STAGE_BYTES + static_cast<size_t>(TILE_WORDS) * 4;
+    return static_cast<size_t>(stages) * STAGE_BYTES + static_cast<size_t>(XCH_WORDS) * 4;
   }
 };
+
+// resident CTAs per SM the register allocation is sized for
+template <int N>
+struct PipeOcc { static constexpr int value = (N == 8) ? 4 : 3; };
 
 // Read row r (N pixels) of block lb from a staged unit with 128-bit shared
 // loads.  `valid` = number of valid pixels of this block's rows (N unless
@@ -120,132 +107,438 @@ __device__ __forceinline__ void stage_read_row(const unsigned char* stage, int l
   }
 }
 
-// The W rows of this thread's slab of block lb.
-template <int N, typename InT>
-__device__ __forceinline__ void stage_read_rows(const unsigned char* stage, int lb, int p, int valid,
-                                                int (&v)[Geo<N>::W][N]) {
-#pragma unroll
-  for (int k = 0; k < Geo<N>::W; ++k) stage_read_row<N, InT>(stage, lb, p * Geo<N>::W + k, valid, v[k]);
+__device__ __forceinline__ void st_v4(int* p, const int* v) {
+  *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void ld_v4(const int* p, int* v) {
+  const int4 q = *reinterpret_cast<const int4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
-// Slab transposes for the pipe kernels (tile per block at lb * TILE_STRIDE).
-// JCW = number of leading columns (rows -> cols) or rows (cols -> rows) that
-// carry data; the rest is known to be zero or unused.
-template <int N, int JCW>
-__device__ __forceinline__ void pipe_rows_to_cols(int* tiles, int lb, int p, int (&v)[Geo<N>::W][N]) {
-  typedef Geo<N> G;
-  if constexpr (G::P == 1) {
-    rows_to_cols<N>(nullptr, 0, 0, v);
-  } else {
-    constexpr int TS = PipeGeo<N, int16_t>::TILE_STRIDE;
-    constexpr int CHW = (JCW + 3) / 4;            // chunks that carry data
-    int* tile = tiles + lb * TS;
+// ---------------------------------------------------------------------------
+// The 8 x 8 core: forward rows / columns, zonal mask, kept coefficients,
+// inverse columns / rows.  v[i][j] holds row i on entry and on exit.  E is the
+// compile-time extent (rows / columns >= E are never kept).  With CT_MASK
+// (N = 8 and a compile-time r) the mask itself is a constant.
+// ---------------------------------------------------------------------------
+template <int N, class P, int CONV, int E, bool CT_MASK, int RFIX>
+__device__ __forceinline__ void core8(int (&v)[8][8], unsigned long long m, int32_t* kept, int q) {
+  typedef Ops<8, P, CONV> O;
 #pragma unroll
-    for (int k = 0; k < G::W; ++k) {
-      const int r = p * G::W + k;
+  for (int i = 0; i < 8; ++i) O::fwd_row(v[i]);
+  rows_to_cols<8>(nullptr, 0, 0, v);            // v[k][i]: column k
 #pragma unroll
-      for (int c = 0; c < CHW; ++c) {
-        const int cs = c ^ G::swz(r);
-        *reinterpret_cast<int4*>(tile + r * N + 4 * cs) =
-            make_int4(v[k][4 * c], v[k][4 * c + 1], v[k][4 * c + 2], v[k][4 * c + 3]);
-      }
+  for (int k = 0; k < 8; ++k) {
+    if (k < E) {
+      O::fwd_col(v[k]);
+#pragma unroll
+      for (int i = E; i < 8; ++i) v[k][i] = 0;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[k][i] = 0;
     }
-    __syncwarp();
-    const int c = (p * G::W) >> 2, off = (p * G::W) & 3;
-    const bool has = p * G::W < JCW;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int* src = tile + i * N + 4 * (c ^ G::swz(i)) + off;
-      if constexpr (G::W == 4) {
-        int4 q = has ? *reinterpret_cast<const int4*>(src) : make_int4(0, 0, 0, 0);
-        v[0][i] = q.x; v[1][i] = q.y; v[2][i] = q.z; v[3][i] = q.w;
-      } else {
-        int2 q = has ? *reinterpret_cast<const int2*>(src) : make_int2(0, 0);
-        v[0][i] = q.x; v[1][i] = q.y;
-      }
-    }
-    __syncwarp();
   }
+  const unsigned long long mk = CT_MASK ? sub_mask(8, RFIX > 0 ? RFIX : 64, 0) : m;
+#pragma unroll
+  for (int k = 0; k < E; ++k)
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      if (!((mk >> (k * 8 + i)) & 1ull)) v[k][i] = 0;
+  if (kept != nullptr) {
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+#pragma unroll
+      for (int i = 0; i < E; ++i)
+        if ((mk >> (k * 8 + i)) & 1ull)
+          kept[zigzag_pos(N, sub_row_of(N, q, i), sub_col_of(N, q, k))] = v[k][i] >> O::FWD_SHIFT;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (k < E) O::inv_col(v[k]);
+  rows_to_cols<8>(nullptr, 0, 0, v);            // back to rows
+#pragma unroll
+  for (int i = 0; i < 8; ++i) O::inv_row(v[i]);
 }
 
-template <int N, int JCW>
-__device__ __forceinline__ void pipe_cols_to_rows(int* tiles, int lb, int p, int (&v)[Geo<N>::W][N]) {
-  typedef Geo<N> G;
-  if constexpr (G::P == 1) {
-    rows_to_cols<N>(nullptr, 0, 0, v);
-  } else {
-    constexpr int TS = PipeGeo<N, int16_t>::TILE_STRIDE;
-    constexpr int CHW = (JCW + 3) / 4;
-    int* tile = tiles + lb * TS;
-    const int c = (p * G::W) >> 2, off = (p * G::W) & 3;
-    if (p * G::W < JCW) {
+// ---------------------------------------------------------------------------
+// Per-N unit bodies.  Each computes 4Z for the rows the thread owns, stores
+// the reconstruction and returns the float squared error of those rows.
+// ---------------------------------------------------------------------------
+struct UnitPos {
+  int img, by, bx;
+  bool active;
+  int valid;          // valid pixels of the block's rows
+  bool fast;          // interior block: all N rows and columns valid, aligned output
+  float* orow0;       // output row 0 of the block
+};
+
+// squared error of one staged row against a packed reconstruction row
+template <int N, typename InT>
+__device__ __forceinline__ f32x2 row_error(const InT* row, const f32x2 (&rec2)[N / 2], f32x2 acc2) {
+  const f32x2 neg1 = pk2(-1.f, -1.f);
+  if constexpr (sizeof(InT) == 2) {
+    const f32x2 mg = pk2(-kMagicI16, -kMagicI16);
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        int* dst = tile + i * N + 4 * (c ^ G::swz(i)) + off;
-        if constexpr (G::W == 4) *reinterpret_cast<int4*>(dst) = make_int4(v[0][i], v[1][i], v[2][i], v[3][i]);
-        else *reinterpret_cast<int2*>(dst) = make_int2(v[0][i], v[1][i]);
+    for (int c = 0; c < N / 8; ++c) {
+      const uint4 q = lds_v4(row + 8 * c);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const f32x2 ref = add2(pk2(i16lo_magic(w[t]), i16hi_magic(w[t])), mg);
+        const f32x2 e = fma2(ref, neg1, rec2[4 * c + t]);
+        acc2 = fma2(e, e, acc2);
       }
     }
-    __syncwarp();
+  } else {
+    const f32x2 mg = pk2(-kMagicU8, -kMagicU8);
 #pragma unroll
-    for (int k = 0; k < G::W; ++k) {
-      const int r = p * G::W + k;
+    for (int c = 0; c < N / 8; ++c) {
+      const uint2 q = *reinterpret_cast<const uint2*>(row + 8 * c);
+      const uint32_t w[2] = {q.x, q.y};
 #pragma unroll
-      for (int cc = 0; cc < G::CH; ++cc) {
-        if (cc < CHW) {
-          const int4 q = *reinterpret_cast<const int4*>(tile + r * N + 4 * (cc ^ G::swz(r)));
-          v[k][4 * cc] = q.x; v[k][4 * cc + 1] = q.y; v[k][4 * cc + 2] = q.z; v[k][4 * cc + 3] = q.w;
-        } else {
-          v[k][4 * cc] = 0; v[k][4 * cc + 1] = 0; v[k][4 * cc + 2] = 0; v[k][4 * cc + 3] = 0;
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const f32x2 ref = add2(pk2(u8_magic(w[t], 2 * h), u8_magic(w[t], 2 * h + 1)), mg);
+          const f32x2 e = fma2(ref, neg1, rec2[4 * c + 2 * t + h]);
+          acc2 = fma2(e, e, acc2);
+        }
+    }
+  }
+  return acc2;
+}
+
+// Store row r of the block's reconstruction (4Z in x) and return its squared
+// error against the staged input.  Interior blocks take the check-free path.
+template <int N, typename InT>
+__device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
+                                           int lb, int r, const int (&x)[N]) {
+  typedef PipeGeo<N, InT> PG;
+  const f32x2 sc2 = pk2(a.scale, a.scale);
+  f32x2 rec2[N / 2];
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j)
+    rec2[j] = mul2(pk2(static_cast<float>(x[2 * j]), static_cast<float>(x[2 * j + 1])), sc2);
+  float rec[N];
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) unpk2(rec2[j], rec[2 * j], rec[2 * j + 1]);
+  const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
+  if (up.fast) {
+    float* orow = up.orow0 + static_cast<long long>(r) * a.out_pitch;
+#pragma unroll
+    for (int c = 0; c < N / 4; ++c)
+      __stcs(reinterpret_cast<float4*>(orow + 4 * c),
+             make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2], rec[4 * c + 3]));
+    if (a.partial == nullptr) return 0.f;
+    float lo, hi;
+    unpk2(row_error<N, InT>(row, rec2, pk2(0.f, 0.f)), lo, hi);
+    return lo + hi;
+  }
+  const int gy = up.by * N + r;
+  if (!up.active || gy >= a.height) return 0.f;
+  float* orow = up.orow0 + static_cast<long long>(r) * a.out_pitch;
+  if (up.valid == N && a.out_vec) {
+#pragma unroll
+    for (int c = 0; c < N / 4; ++c)
+      __stcs(reinterpret_cast<float4*>(orow + 4 * c),
+             make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2], rec[4 * c + 3]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j < up.valid) orow[j] = rec[j];
+  }
+  if (a.partial == nullptr) return 0.f;
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if (j < up.valid) {
+      const float e = rec[j] - static_cast<float>(row[min(j, up.valid - 1)]);
+      acc = fmaf(e, e, acc);
+    }
+  return acc;
+}
+
+__device__ __forceinline__ int32_t* kept_ptr(const BlockArgs& a, const UnitPos& up) {
+  if (a.kept == nullptr || !up.active) return nullptr;
+  return static_cast<int32_t*>(a.kept) +
+         (static_cast<long long>(up.img) * a.blocks_per_img + static_cast<long long>(up.by) * a.nbx + up.bx) * a.r;
+}
+
+template <int N, class P, int CONV, typename InT, int RFIX>
+struct UnitBody;
+
+// N = 8: one thread, one block.
+template <class P, int CONV, typename InT, int RFIX>
+struct UnitBody<8, P, CONV, InT, RFIX> {
+  static constexpr int E = RFIX > 0 ? zonal_extent(8, RFIX) : 8;
+  static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
+                                              int* /*xch*/, int /*lane*/, int lb) {
+    int v[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) stage_read_row<8, InT>(stage, lb, i, up.valid, v[i]);
+    core8<8, P, CONV, E, (RFIX > 0), RFIX>(v, a.slab_mask[0], kept_ptr(a, up), 0);
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc += store_row<8, InT>(a, up, stage, lb, i, v[i]);
+    return acc;
+  }
+};
+
+// N = 16: thread (block lb, p < 4) owns rows {p, 7-p, 8+p, 15-p}; in the
+// core it owns sub-block s = p.  Exchange buffer per block: 16-byte chunks
+// [s 4][row 8][ch 2], blocks 65 chunks apart (the odd stride spreads the 8
+// blocks of one quarter warp over all bank groups).
+template <class P, int CONV, typename InT, int RFIX>
+struct UnitBody<16, P, CONV, InT, RFIX> {
+  static constexpr int E = RFIX > 0 ? (zonal_extent(16, RFIX) + 1) / 2 : 8;
+  // word offset of chunk (s, row, ch) within a block
+  static constexpr int off(int s, int row, int ch) { return 4 * ((s * 8 + row) * 2 + ch); }
+  static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
+                                              int* xch, int lane, int lb) {
+    const int p = lane >> 3, lbw = lane & 7;
+    int* buf = xch + lbw * 65 * 4;
+    int* rp = buf + 8 * p;              // row p of every sub-block
+    int* rq = buf + 8 * (7 - p);        // row 7-p
+    {
+      const int rows[4] = {p, 7 - p, 8 + p, 15 - p};
+      int h[4][2][8];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        int x[16];
+        stage_read_row<16, InT>(stage, lb, rows[t], up.valid, x);
+        madd<16>(x, h[t][0], h[t][1]);                 // horizontal fold
+      }
+      // vertical fold: top row p = r0 + r3, top row 7-p = r1 + r2,
+      //                bottom row p = r1 - r2, bottom row 7-p = r0 - r3
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        int g[4][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          g[0][j] = h[0][b][j] + h[3][b][j];
+          g[1][j] = h[1][b][j] + h[2][b][j];
+          g[2][j] = h[1][b][j] - h[2][b][j];
+          g[3][j] = h[0][b][j] - h[3][b][j];
+        }
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          st_v4(rp + off(0 + b, 0, ch), &g[0][4 * ch]);
+          st_v4(rq + off(0 + b, 0, ch), &g[1][4 * ch]);
+          st_v4(rp + off(2 + b, 0, ch), &g[2][4 * ch]);
+          st_v4(rq + off(2 + b, 0, ch), &g[3][4 * ch]);
         }
       }
     }
     __syncwarp();
+    {
+      const int s = p;
+      int* sb = buf + off(s, 0, 0);
+      int v[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) ld_v4(sb + off(0, i, ch), &v[i][4 * ch]);
+      __syncwarp();
+      core8<16, P, CONV, E, false, RFIX>(v, a.slab_mask[s], kept_ptr(a, up), s);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) st_v4(sb + off(0, i, ch), &v[i][4 * ch]);
+    }
+    __syncwarp();
+    float acc = 0.f;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      // vertical unfold: half 0 yields rows p and 15-p, half 1 rows 7-p and 8+p:
+      //   x_p = top_p + bot_{7-p},      x_{15-p} = top_p - bot_{7-p}
+      //   x_{7-p} = top_{7-p} + bot_p,  x_{8+p} = top_{7-p} - bot_p
+      int* rt = half == 0 ? rp : rq;
+      int* rb = half == 0 ? rq : rp;
+      int lo_s[8], hi_s[8], lo_d[8], hi_d[8];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        int t[8], u[8];
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          ld_v4(rt + off(0 + b, 0, ch), &t[4 * ch]);
+          ld_v4(rb + off(2 + b, 0, ch), &u[4 * ch]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (b == 0) { lo_s[j] = t[j] + u[j]; lo_d[j] = t[j] - u[j]; }
+          else { hi_s[j] = t[j] + u[j]; hi_d[j] = t[j] - u[j]; }
+        }
+      }
+      int xs[16], xd[16];
+      madd_join<16>(lo_s, hi_s, xs);        // horizontal unfold
+      madd_join<16>(lo_d, hi_d, xd);
+      const int r0 = half == 0 ? p : 7 - p;
+      acc += store_row<16, InT>(a, up, stage, lb, r0, xs);
+      acc += store_row<16, InT>(a, up, stage, lb, 15 - r0, xd);
+    }
+    __syncwarp();
+    return acc;
   }
-}
+};
 
-// resident CTAs per SM the register allocation is sized for
-template <int N>
-struct PipeOcc { static constexpr int value = (N == 8) ? 4 : 3; };
+// N = 32: thread (block lb, p < 16) owns rows {p, 31-p}; in the core it owns
+// sub-block q = hr*8 + ar*4 + c (hr: first vertical fold half, ar: second,
+// c = h*2 + a' for the two horizontal folds).  Per block, 288 chunks of 16
+// bytes hold, in turn:
+//   layout 1 (after the first vertical fold): chunk (hr*16 + row)*9 + 2c + ch
+//   layout 2 (core output):                    chunk q*17 + 2row + (row >> 2) + ch
+// The odd strides / the pad chunk after row 3 make every access pattern
+// below bank-conflict free with plain base + constant addressing.
+template <class P, int CONV, typename InT, int RFIX>
+struct UnitBody<32, P, CONV, InT, RFIX> {
+  static constexpr int E = RFIX > 0 ? (zonal_extent(32, RFIX) + 3) / 4 : 8;
+  static constexpr int l2(int q, int row, int ch) { return 4 * (q * 17 + 2 * row + (row >> 2) + ch); }
+  static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
+                                              int* xch, int lane, int lb) {
+    const int p = lane & 15, lbw = lane >> 4;
+    int* buf = xch + lbw * 288 * 4;
+    {
+      int hc[2][4][8];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        int x[32], lo[16], hi[16];
+        stage_read_row<32, InT>(stage, lb, t == 0 ? p : 31 - p, up.valid, x);
+        madd<32>(x, lo, hi);                       // horizontal fold, first level
+        madd<16>(lo, hc[t][0], hc[t][1]);          // second level: c = h*2 + a'
+        madd<16>(hi, hc[t][2], hc[t][3]);
+      }
+      // first vertical fold: half 0 row p = x_p + x_{31-p}, half 1 row 15-p = x_p - x_{31-p}
+      int* w0 = buf + 4 * (p * 9);
+      int* w1 = buf + 4 * ((16 + 15 - p) * 9);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        int s0[8], s1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { s0[j] = hc[0][c][j] + hc[1][c][j]; s1[j] = hc[0][c][j] - hc[1][c][j]; }
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          st_v4(w0 + 4 * (2 * c + ch), &s0[4 * ch]);
+          st_v4(w1 + 4 * (2 * c + ch), &s1[4 * ch]);
+        }
+      }
+    }
+    __syncwarp();
+    {
+      const int q = p, hr = q >> 3, ar = (q >> 2) & 1, c = q & 3;
+      const int sgn = ar ? -1 : 1;
+      // second vertical fold within half hr:
+      //   ar = 0: row i = H[i] + H[15-i];  ar = 1: row i = H[7-i] - H[8+i]
+      const int* hb = buf + 4 * (hr * 16 * 9 + 2 * c);
+      const int* pa = hb + 4 * 9 * (ar ? 7 : 0);
+      const int* pb = hb + 4 * 9 * (ar ? 8 : 15);
+      const int step = ar ? -4 * 9 : 4 * 9;        // pa walks down (ar = 1) or up, pb the other way
+      int v[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          int t[4], u[4];
+          ld_v4(pa + 4 * ch, t);
+          ld_v4(pb + 4 * ch, u);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[i][4 * ch + e] = t[e] + sgn * u[e];
+        }
+        pa += step;
+        pb -= step;
+      }
+      __syncwarp();
+      core8<32, P, CONV, E, false, RFIX>(v, a.slab_mask[q], kept_ptr(a, up), q);
+      int* qb = buf + l2(q, 0, 0);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) st_v4(qb + l2(0, i, ch), &v[i][4 * ch]);
+    }
+    __syncwarp();
+    // second vertical unfold (within each half), then the first:
+    //   H[m] = top_m + bot_{7-m} (m < 8),  H[8+k] = top_{7-k} - bot_k
+    //   x_p = H0[p] + H1[15-p],  x_{31-p} = H0[p] - H1[15-p]
+    int hc0[4][8], hc1[4][8];
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int m = hr == 0 ? p : 15 - p;
+      const int rt = m < 8 ? m : 15 - m, rb = m < 8 ? 7 - m : m - 8;
+      const int sg = m < 8 ? 1 : -1;
+      const int* bt = buf + l2(0, rt, 0);
+      const int* bb = buf + l2(0, rb, 0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int qt = hr * 8 + c, qb = hr * 8 + 4 + c;
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          int t[4], u[4];
+          ld_v4(bt + 4 * (qt * 17 + ch), t);
+          ld_v4(bb + 4 * (qb * 17 + ch), u);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (hr == 0) hc0[c][4 * ch + e] = t[e] + sg * u[e];
+            else hc1[c][4 * ch + e] = t[e] + sg * u[e];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      int cc[4][8];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cc[c][j] = t == 0 ? hc0[c][j] + hc1[c][j] : hc0[c][j] - hc1[c][j];
+      int lo[16], hi[16], x[32];
+      madd_join<16>(cc[0], cc[1], lo);             // horizontal unfold, second level
+      madd_join<16>(cc[2], cc[3], hi);
+      madd_join<32>(lo, hi, x);                    // first level
+      acc += store_row<32, InT>(a, up, stage, lb, t == 0 ? p : 31 - p, x);
+    }
+    return acc;
+  }
+};
 
+// ---------------------------------------------------------------------------
+// The persistent kernel
+// ---------------------------------------------------------------------------
 template <int N, class P, int CONV, typename InT, int RFIX, int STAGES>
 __global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(const PipeArgs pa) {
-  typedef Geo<N> G;
   typedef PipeGeo<N, InT> PG;
-  typedef Ops<N, P, CONV> O;
-  constexpr int W = G::W;
-  // rows and columns that can hold kept coefficients
-  constexpr int JC = RFIX > 0 ? zonal_extent(N, RFIX) : N;
+  constexpr int NW = kThreads / 32;
   const BlockArgs& a = pa.b;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  int* tiles = reinterpret_cast<int*>(smem + STAGES * PG::STAGE_BYTES);
+  int* xch_all = reinterpret_cast<int*>(smem + STAGES * PG::STAGE_BYTES);
   __shared__ __align__(8) uint64_t full[STAGES];
-  __shared__ float wsum[2][kThreads / 32];
-  __shared__ int stop;
+  __shared__ int done[STAGES];           // warps that finished the stage's current unit
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int lb, p;
-  PG::lane_map(tid, lb, p);
+  int* xch = xch_all + warp * PG::XCH_WARP_WORDS;
+  // block of this thread within the unit
+  const int lb = (N == 8) ? tid : (N == 16 ? warp * 8 + (lane & 7) : warp * 2 + (lane >> 4));
   const uint64_t policy = policy_evict_first();
   const long long G_ = gridDim.x;
   const int es = static_cast<int>(sizeof(InT));
 
   if (tid == 0) {
 #pragma unroll
-    for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      done[s] = 0;
+    }
     fence_mbar_init();
-    stop = 0;
   }
   __syncthreads();
 
-  // warp 0 issues the copies of one unit into stage s
+  // one whole warp issues the copies of unit u into stage s
   auto issue = [&](long long u, int s) {
-    const int img = static_cast<int>(u / pa.units_per_img);
-    const long long rem = u - static_cast<long long>(img) * pa.units_per_img;
-    const int by = static_cast<int>(rem / pa.units_per_row);
-    const int seg = static_cast<int>(rem - static_cast<long long>(by) * pa.units_per_row);
-    const int x0 = seg * PG::WPX;
+    uint32_t rem, seg;
+    const int img = static_cast<int>(fdiv(static_cast<uint32_t>(u), pa.div_img, rem));
+    const int by = static_cast<int>(fdiv(rem, pa.div_row, seg));
+    const int x0 = static_cast<int>(seg) * PG::WPX;
     const uint32_t bytes = static_cast<uint32_t>(min(PG::WPX, a.width - x0) * es);
     if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes * N);
     __syncwarp();
@@ -264,124 +557,47 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(c
     }
   }
 
-  for (int it = 0;; ++it) {
+  bool failed = false;
+  int it = 0;
+  for (;; ++it) {
     const long long u = blockIdx.x + it * G_;
     if (u >= pa.total_units) break;
     const int s = it % STAGES;
     const uint32_t parity = static_cast<uint32_t>((it / STAGES) & 1);
-    const bool ok = mbar_wait_bounded(&full[s], parity, pa.wait_limit);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(pa.err, 1);
-        stop = 1;
-      }
-      break;
-    }
+    if (!mbar_wait_bounded(&full[s], parity, pa.wait_limit)) { failed = true; break; }
     const unsigned char* stage = smem + s * PG::STAGE_BYTES;
 
-    // unit -> image, block row, first block
-    const int img = static_cast<int>(u / pa.units_per_img);
-    const long long rem = u - static_cast<long long>(img) * pa.units_per_img;
-    const int by = static_cast<int>(rem / pa.units_per_row);
-    const int seg = static_cast<int>(rem - static_cast<long long>(by) * pa.units_per_row);
-    const int bx = seg * PG::S + lb;
-    const bool active = bx < a.nbx;
-    const int x0 = bx * N;
-    const int valid = active ? min(N, a.width - x0) : N;
+    UnitPos up;
+    uint32_t rem, seg;
+    up.img = static_cast<int>(fdiv(static_cast<uint32_t>(u), pa.div_img, rem));
+    up.by = static_cast<int>(fdiv(rem, pa.div_row, seg));
+    up.bx = static_cast<int>(seg) * PG::S + lb;
+    up.active = up.bx < a.nbx;
+    up.valid = up.active ? min(N, a.width - up.bx * N) : N;
+    up.fast = up.active && up.valid == N && a.out_vec && (up.by + 1) * N <= a.height;
+    up.orow0 = a.out + static_cast<long long>(up.img) * a.out_bstride +
+               static_cast<long long>(up.by) * N * a.out_pitch + up.bx * N;
 
-    int v[W][N];
-    stage_read_rows<N, InT>(stage, lb, p, valid, v);
-    if (!active) {
-#pragma unroll
-      for (int k = 0; k < W; ++k)
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[k][j] = 0;
-    }
+    float acc = UnitBody<N, P, CONV, InT, RFIX>::run(a, up, stage, xch, lane, lb);
 
-    // forward row pass; only columns < JC are ever used
-#pragma unroll
-    for (int k = 0; k < W; ++k) O::fwd_row(v[k]);
-    pipe_rows_to_cols<N, JC>(tiles, lb, p, v);
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      O::fwd_col(v[k]);
-#pragma unroll
-      for (int i = JC; i < N; ++i) v[k][i] = 0;     // rows >= JC never kept
-    }
-    // zonal mask
-    if constexpr (RFIX > 0 && G::P == 1) {
-      constexpr unsigned long long m = slab_mask_ct(N, RFIX, 0);
-#pragma unroll
-      for (int k = 0; k < W; ++k)
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-          if (!((m >> (k * N + i)) & 1ull)) v[k][i] = 0;
-    } else {
-      const unsigned long long m = a.slab_mask[p];
-#pragma unroll
-      for (int k = 0; k < W; ++k)
-#pragma unroll
-        for (int i = 0; i < JC; ++i)
-          if (!((m >> (k * N + i)) & 1ull)) v[k][i] = 0;
-    }
-    if (a.kept != nullptr && active) {
-      BlockPos bp;
-      bp.img = img; bp.lb = lb; bp.p = p; bp.by = by; bp.bx = bx;
-      bp.gb = static_cast<long long>(by) * a.nbx + bx; bp.active = true;
-      store_kept<N>(a, bp, v, O::FWD_SHIFT);
-    }
-#pragma unroll
-    for (int k = 0; k < W; ++k) O::inv_col(v[k]);
-    pipe_cols_to_rows<N, JC>(tiles, lb, p, v);
-#pragma unroll
-    for (int k = 0; k < W; ++k) O::inv_row(v[k]);
-
-    // store the reconstruction, squared error against the staged input
-    float acc = 0.f;
-    float* out = a.out + static_cast<long long>(img) * a.out_bstride;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      const int gy = by * N + p * W + k;
-      if (!active || gy >= a.height) continue;
-      float rec[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) rec[j] = static_cast<float>(v[k][j]) * a.scale;
-      float* orow = out + static_cast<long long>(gy) * a.out_pitch + x0;
-      if (valid == N && a.out_vec) {
-#pragma unroll
-        for (int c = 0; c < N / 4; ++c)
-          __stcs(reinterpret_cast<float4*>(orow + 4 * c),
-                 make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2], rec[4 * c + 3]));
-      } else {
-#pragma unroll
-        for (int j = 0; j < N; ++j)
-          if (j < valid) orow[j] = rec[j];
-      }
-      if (a.partial != nullptr) {
-        int ref[1][N];
-        stage_read_row<N, InT>(stage, lb, p * W + k, valid, ref[0]);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          if (j < valid) {
-            const float e = rec[j] - static_cast<float>(ref[0][j]);
-            acc = fmaf(e, e, acc);
-          }
-        }
-      }
-    }
     if (a.partial != nullptr) {
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) wsum[it & 1][warp] = acc;
+      if (lane == 0) a.partial[u * NW + warp] = static_cast<double>(acc);
     }
-    __syncthreads();   // the stage is consumed; wsum is complete
-    if (tid == 0 && a.partial != nullptr) {
-      double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) t += static_cast<double>(wsum[it & 1][w]);
-      a.partial[u] = t;
+    // release the stage; the last warp to do so refills it with unit u + STAGES*G
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+      __threadfence_block();                 // this warp's reads of the stage come first
+      last = atomicAdd(&done[s], 1) == NW - 1;
+      if (last) {
+        done[s] = 0;
+        __threadfence_block();
+      }
     }
-    if (warp == 0) {
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
       const long long un = u + STAGES * G_;
       if (un < pa.total_units) {
         fence_proxy_async_smem();
@@ -390,16 +606,16 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(c
     }
   }
 
-  __syncthreads();
-  if (stop) {
-    // a stage never completed: wait (bounded) for the copies that did get
-    // issued so that none is still writing this CTA's shared memory
-    if (tid == 0) {
-      for (int s = 0; s < STAGES; ++s) {
-        for (int ph = 0; ph < 2; ++ph) (void)mbar_wait_bounded(&full[s], ph, pa.wait_limit);
-      }
+  if (failed) {
+    if (lane == 0) atomicOr(pa.err, 1);
+    // wait (bounded) for copies that may still be landing in this CTA's
+    // stages, so that none writes shared memory after the CTA exits
+    for (int k = 0; k < STAGES; ++k) {
+      const int itk = it + k;
+      const long long uk = blockIdx.x + static_cast<long long>(itk) * G_;
+      if (uk >= pa.total_units) break;
+      (void)mbar_wait_bounded(&full[itk % STAGES], static_cast<uint32_t>((itk / STAGES) & 1), pa.wait_limit);
     }
-    __syncthreads();
   }
 }
 
@@ -426,13 +642,8 @@ int occupancy_pipe() {
   return n;
 }
 
-}  // namespace cdct
-
-namespace cdct {
-
-// Launch the pipe kernel with the compile-time r among Rs that equals r, or
-// the runtime-mask version; the grid is the resident CTA count, capped by
-// the number of units.
+// Launch with the compile-time r among Rs that equals r, or the runtime-mask
+// version; the grid is the resident CTA count, capped by the number of units.
 template <int N, class P, int CONV, typename InT, int STAGES>
 int pipe_launch_r(const PipeArgs& pa, int r, int num_sms, void* stream) {
   (void)r;
