@@ -140,6 +140,29 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
                                double* psnr_db, void* workspace, size_t workspace_bytes,
                                void* stream);
 
+/* The fused call of cdct_fwd_zonal_inv for callers that cannot allocate
+ * device memory: code that must run with the buffers it already owns (a
+ * fixed memory budget, no device allocator of its own, or a host that may
+ * not call cudaMalloc while it runs).  It takes no workspace; the error
+ * partials go to a scratch array of fixed size (1 MiB) that the library
+ * holds in static device memory, on every GPU that loads it, until the
+ * process exits.  The paper has no counterpart: this is an interface
+ * choice, not part of the method.
+ *  - Limit: with psnr_db set, a call needing more than 1 MiB of partials
+ *    (cdct_workspace_size() > 1 MiB, e.g. more than about a hundred
+ *    1920x1080 planes in one call) is rejected with CDCT_EINVAL; without
+ *    psnr_db no scratch is used.
+ *  - Set-up: the first call on a device (with that device current) looks up
+ *    the scratch's device address; make that first call before any stream
+ *    capture.
+ *  - The scratch is shared by every call on the device: calls that overlap
+ *    on the GPU (other streams, other threads) race on it and must be
+ *    ordered by the caller.  Nothing in it has to start at zero.
+ *  - No device memory is allocated or freed by this call. */
+cdct_status cdct_fwd_zonal_inv_noalloc(cdct_plan plan, const cdct_image* in, int r, float* recon,
+                                       int64_t recon_pitch, int64_t recon_batch_stride, void* kept,
+                                       double* psnr_db, void* stream);
+
 /* Synchronise `stream` and report whether a kernel of this library gave up
  * a bounded wait on the current device since the last check (the fused
  * kernel waits, with a time limit of about one second, for the bulk copies

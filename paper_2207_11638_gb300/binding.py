@@ -24,6 +24,7 @@ EXPORTS = (
     "cdct_plan_create", "cdct_plan_destroy", "cdct_block_count", "cdct_workspace_size",
     "cdct_forward", "cdct_zonal", "cdct_inverse", "cdct_psnr", "cdct_fwd_zonal_inv",
     "cdct_matrix", "cdct_last_error", "cdct_version", "cdct_check_device",
+    "cdct_fwd_zonal_inv_noalloc",
 )
 
 
@@ -65,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cdct_last_error": (ctypes.c_char_p, []),
         "cdct_version": (ctypes.c_char_p, []),
         "cdct_check_device": (ctypes.c_int, [vp]),
+        "cdct_fwd_zonal_inv_noalloc": (ctypes.c_int, [vp, img_p, ctypes.c_int, vp, i64, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +249,28 @@ class Plan:
             ws.numel() * ws.element_size() if ws is not None else 0,
             stream_handle(stream)))
         return out, kp, ps
+
+
+def fwd_zonal_inv_noalloc(plan, img, r, out=None, kept=False, psnr=True, stream=None):
+    """cdct_fwd_zonal_inv_noalloc: the fused call without a workspace (the
+    library's fixed static scratch holds the error partials)."""
+    torch = _torch()
+    d = image_desc(img)
+    n = plan.n
+    if out is None:
+        out = torch.empty((d.batch, d.height, d.width), dtype=torch.float32, device=img.device)
+    o3 = out if out.dim() == 3 else out.unsqueeze(0)
+    kp = None
+    if kept:
+        nby, nbx = -(-d.height // n), -(-d.width // n)
+        kp = torch.empty((d.batch, nby, nbx, r), dtype=plan._coeff_dtype(), device=img.device)
+    ps = torch.empty(d.batch, dtype=torch.float64, device=img.device) if psnr else None
+    check(lib().cdct_fwd_zonal_inv_noalloc(
+        plan.handle, ctypes.byref(d), r, o3.data_ptr(), o3.stride(1),
+        o3.stride(0) if d.batch > 1 else d.height * o3.stride(1),
+        kp.data_ptr() if kp is not None else None,
+        ps.data_ptr() if ps is not None else None, stream_handle(stream)))
+    return out, kp, ps
 
 
 _PSNR_PLAN = None

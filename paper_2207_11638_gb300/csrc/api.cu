@@ -18,6 +18,13 @@ using namespace cdct;
 // cdct_check_device); one per device, reached through its symbol address.
 static __device__ int g_device_error;
 
+// Scratch of cdct_fwd_zonal_inv_noalloc: room for the per-CTA / per-warp
+// error partials of one call.  Device code reaches it through the address
+// the host fetches once per device (host code must not use the symbol
+// itself: in host code it names a host-side stand-in, not device memory).
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 17;   // 1 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
 struct cdct_plan_s {
   int n, variant, conv;
   double T[32 * 32];
@@ -52,6 +59,7 @@ constexpr int kMaxDevices = 64;
 struct DeviceInfo {
   int sms = 0;
   int* err = nullptr;
+  double* noalloc_scratch = nullptr;   // device address of g_noalloc_scratch
 };
 DeviceInfo g_dev[kMaxDevices];
 
@@ -394,6 +402,39 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
     if (rc) return cuda_fail(rc, "psnr finalize launch");
   }
   return CDCT_OK;
+}
+
+cdct_status cdct_fwd_zonal_inv_noalloc(cdct_plan plan, const cdct_image* in, int r, float* recon,
+                                       int64_t recon_pitch, int64_t recon_batch_stride, void* kept, double* psnr_db,
+                                       void* stream) {
+  if (plan == nullptr) return fail(CDCT_EINVAL, "null plan");
+  cdct_status st = check_image(in, "fwd_zonal_inv_noalloc");
+  if (st != CDCT_OK) return st;
+  size_t need = 0;
+  if (psnr_db != nullptr) {
+    need = partial_count(plan, in->width, in->height, in->batch) * sizeof(double);
+    if (need > kNoAllocScratchDoubles * sizeof(double))
+      return fail(CDCT_EINVAL, "fwd_zonal_inv_noalloc: this call needs " + std::to_string(need) +
+                                   " bytes of error partials, more than the fixed " +
+                                   std::to_string(kNoAllocScratchDoubles * sizeof(double)) +
+                                   "-byte scratch; use cdct_fwd_zonal_inv with a workspace");
+  }
+  // set-up, once per device with that device current: the scratch's device address
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(static_cast<int>(e), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(CDCT_EUNSUPPORTED, "device ordinal out of range");
+  DeviceInfo& d = g_dev[dev];
+  if (d.noalloc_scratch == nullptr) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(static_cast<int>(e), "cudaGetSymbolAddress(scratch)");
+    d.noalloc_scratch = static_cast<double*>(ptr);
+  }
+  // every partial a call reads is written by the same call, so the scratch
+  // needs no clearing between calls
+  return cdct_fwd_zonal_inv(plan, in, r, recon, recon_pitch, recon_batch_stride, kept, psnr_db, d.noalloc_scratch,
+                            kNoAllocScratchDoubles * sizeof(double), stream);
 }
 
 cdct_status cdct_check_device(void* stream) {
