@@ -140,6 +140,46 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
                                double* psnr_db, void* workspace, size_t workspace_bytes,
                                void* stream);
 
+/* Pipeline tuning of a plan (the autotuner sets it): staging depth of the
+ * fused kernel's input ring (0 = default for N, or 2, 3) and resident CTAs
+ * per SM used for its persistent grid (0 = as many as fit).  Changes the
+ * schedule only, never the results.  Not to be called while another thread
+ * uses the plan. */
+cdct_status cdct_plan_set_tuning(cdct_plan plan, int stages, int ctas_per_sm);
+
+/* ---- Batches of images of uneven sizes (one persistent launch) ----------
+ * A batch lists images of any sizes (device pointers; rows, widths and
+ * pointers 16-byte aligned).  cdct_batch_create validates the list on the
+ * host (an invalid descriptor returns CDCT_EINVAL naming the image) and
+ * builds a descriptor table: the images and the prefix sums of their work
+ * units.  The caller allocates `table_bytes` of device memory for it and
+ * uploads it once with cdct_batch_upload; cdct_batch_fzi then runs the fused
+ * forward -> zonal(r) -> inverse (+ PSNR per image) over every image in one
+ * persistent launch (plus one launch for the PSNRs), which can be captured
+ * in a CUDA graph.  The batch keeps the plan's N, variant and convention;
+ * the plan must outlive it. */
+typedef struct cdct_batch_s* cdct_batch;
+
+typedef struct {
+  const void* data;        /* first pixel (device) */
+  float* recon;            /* first reconstructed pixel (device) */
+  int32_t width, height;
+  int64_t pitch;           /* elements between input rows */
+  int64_t recon_pitch;     /* floats between reconstruction rows */
+} cdct_batch_image;
+
+cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, int n_images, int dtype,
+                              cdct_batch* out);
+cdct_status cdct_batch_destroy(cdct_batch batch);
+/* Device bytes of the table and of the PSNR workspace; total pixels. */
+cdct_status cdct_batch_sizes(cdct_batch batch, size_t* table_bytes, size_t* workspace_bytes,
+                             int64_t* total_pixels);
+/* Copy the table to device_table (16-byte aligned, table_bytes); synchronises `stream`. */
+cdct_status cdct_batch_upload(cdct_batch batch, void* device_table, void* stream);
+/* psnr_db: device array of n_images doubles (NULL to skip, then no workspace is needed). */
+cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, double* psnr_db,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
 /* The fused call of cdct_fwd_zonal_inv for callers that cannot allocate
  * device memory: code that must run with the buffers it already owns (a
  * fixed memory budget, no device allocator of its own, or a host that may

@@ -24,7 +24,8 @@ EXPORTS = (
     "cdct_plan_create", "cdct_plan_destroy", "cdct_block_count", "cdct_workspace_size",
     "cdct_forward", "cdct_zonal", "cdct_inverse", "cdct_psnr", "cdct_fwd_zonal_inv",
     "cdct_matrix", "cdct_last_error", "cdct_version", "cdct_check_device",
-    "cdct_fwd_zonal_inv_noalloc",
+    "cdct_fwd_zonal_inv_noalloc", "cdct_plan_set_tuning", "cdct_batch_create", "cdct_batch_destroy",
+    "cdct_batch_sizes", "cdct_batch_upload", "cdct_batch_fzi",
 )
 
 
@@ -37,6 +38,17 @@ class CdctImage(ctypes.Structure):
         ("pitch", ctypes.c_int64),
         ("batch", ctypes.c_int32),
         ("batch_stride", ctypes.c_int64),
+    ]
+
+
+class CdctBatchImage(ctypes.Structure):
+    _fields_ = [
+        ("data", ctypes.c_void_p),
+        ("recon", ctypes.c_void_p),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("pitch", ctypes.c_int64),
+        ("recon_pitch", ctypes.c_int64),
     ]
 
 
@@ -67,6 +79,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cdct_version": (ctypes.c_char_p, []),
         "cdct_check_device": (ctypes.c_int, [vp]),
         "cdct_fwd_zonal_inv_noalloc": (ctypes.c_int, [vp, img_p, ctypes.c_int, vp, i64, i64, vp, vp, vp]),
+        "cdct_plan_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "cdct_batch_create": (ctypes.c_int, [vp, ctypes.POINTER(CdctBatchImage), ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(vp)]),
+        "cdct_batch_destroy": (ctypes.c_int, [vp]),
+        "cdct_batch_sizes": (ctypes.c_int, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(i64)]),
+        "cdct_batch_upload": (ctypes.c_int, [vp, vp, vp]),
+        "cdct_batch_fzi": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -151,6 +170,11 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    def set_tuning(self, stages: int = 0, ctas_per_sm: int = 0):
+        """Staging depth (0, 2, 3) and resident CTAs per SM (0 = all that fit)."""
+        check(lib().cdct_plan_set_tuning(self._h, stages, ctas_per_sm))
+        self.tuning = (stages, ctas_per_sm)
 
     # -- host tables ---------------------------------------------------------
     def matrix(self, which: int):
@@ -271,6 +295,58 @@ def fwd_zonal_inv_noalloc(plan, img, r, out=None, kept=False, psnr=True, stream=
         kp.data_ptr() if kp is not None else None,
         ps.data_ptr() if ps is not None else None, stream_handle(stream)))
     return out, kp, ps
+
+
+class Batch:
+    """Images of uneven sizes run by one persistent launch (cdct_batch_*).
+
+    ``images``: CUDA tensors [H, W] (uint8 or int16, same dtype, rows
+    contiguous and 16-byte aligned).  Reconstructions are float32 tensors
+    [H, W] allocated here unless given.
+    """
+
+    def __init__(self, plan: Plan, images, recons=None):
+        torch = _torch()
+        self.plan, self.images = plan, list(images)
+        dt = self.images[0].dtype
+        if any(t.dtype != dt for t in self.images):
+            raise ValueError("all images of a batch share one dtype")
+        self.dtype = DTYPES["u8" if dt == torch.uint8 else "i16"]
+        if recons is None:
+            recons = [torch.empty(t.shape, dtype=torch.float32, device=t.device) for t in self.images]
+        self.recons = list(recons)
+        n = len(self.images)
+        descs = (CdctBatchImage * n)()
+        for i, (t, o) in enumerate(zip(self.images, self.recons)):
+            if t.dim() != 2 or t.stride(1) != 1 or o.stride(1) != 1:
+                raise ValueError("batch images must be [H, W] with contiguous rows")
+            descs[i] = CdctBatchImage(t.data_ptr(), o.data_ptr(), t.shape[1], t.shape[0], t.stride(0), o.stride(0))
+        h = ctypes.c_void_p()
+        check(lib().cdct_batch_create(plan.handle, descs, n, self.dtype, ctypes.byref(h)))
+        self._h = h
+        tb, wb, px = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+        check(lib().cdct_batch_sizes(h, ctypes.byref(tb), ctypes.byref(wb), ctypes.byref(px)))
+        dev = self.images[0].device
+        self.pixels = px.value
+        self.table = torch.empty(max(16, tb.value), dtype=torch.uint8, device=dev)
+        self.workspace = torch.empty(max(1, wb.value // 8), dtype=torch.float64, device=dev)
+        self.psnr = torch.empty(n, dtype=torch.float64, device=dev)
+        check(lib().cdct_batch_upload(h, self.table.data_ptr(), stream_handle()))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _LIB is not None:
+            _LIB.cdct_batch_destroy(h)
+            self._h = None
+
+    def run(self, r: int, psnr: bool = True, stream=None):
+        """Fused forward -> zonal(r) -> inverse over every image; returns the
+        per-image PSNR tensor (device) or None."""
+        check(lib().cdct_batch_fzi(self._h, self.table.data_ptr(), r,
+                                   self.psnr.data_ptr() if psnr else None,
+                                   self.workspace.data_ptr() if psnr else None,
+                                   self.workspace.numel() * 8 if psnr else 0, stream_handle(stream)))
+        return self.psnr if psnr else None
 
 
 _PSNR_PLAN = None

@@ -25,13 +25,25 @@ static __device__ int g_device_error;
 constexpr size_t kNoAllocScratchDoubles = size_t(1) << 17;   // 1 MiB
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
+struct cdct_batch_s;
+
 struct cdct_plan_s {
   int n, variant, conv;
+  PipeTuning tuning;
   double T[32 * 32];
   double U[32 * 32];
   double S[32];
   float s_f[32];
   KernelSet ks[2];  // per input dtype
+};
+
+struct cdct_batch_s {
+  const cdct_plan_s* plan;
+  int dtype, n_images;
+  long long total_units;
+  long long total_pixels;
+  size_t table_bytes, prefix_offset;
+  std::string host_table;        // BatchImage[n], padding, int64 unit_prefix[n + 1]
 };
 
 namespace {
@@ -83,10 +95,11 @@ int device_info(DeviceInfo** out) {
   return 0;
 }
 
-int pipe_launch(int n, int variant, int conv, int dtype, const PipeArgs& pa, int r, int sms, void* stream) {
-  if (n == 8) return pipe_launch_n8(variant, conv, dtype, pa, r, sms, stream);
-  if (n == 16) return pipe_launch_n16(variant, conv, dtype, pa, r, sms, stream);
-  return pipe_launch_n32(variant, conv, dtype, pa, r, sms, stream);
+int pipe_launch(int n, int variant, int conv, int dtype, const PipeArgs& pa, int r, int sms, PipeTuning t,
+                void* stream) {
+  if (n == 8) return pipe_launch_n8(variant, conv, dtype, pa, r, sms, t, stream);
+  if (n == 16) return pipe_launch_n16(variant, conv, dtype, pa, r, sms, t, stream);
+  return pipe_launch_n32(variant, conv, dtype, pa, r, sms, t, stream);
 }
 
 // Apply one of the library's 1-D operators to every unit vector (host side).
@@ -221,6 +234,8 @@ cdct_status cdct_plan_create(int n, int variant, uint32_t flags, cdct_plan* out)
   cdct_plan_s* p = new (std::nothrow) cdct_plan_s();
   if (p == nullptr) return fail(CDCT_ENOMEM, "plan allocation failed");
   p->n = n;
+  p->tuning.stages = 0;
+  p->tuning.ctas_per_sm = 0;
   p->variant = variant;
   p->conv = (flags & CDCT_CONV_TRANSPOSE) ? 1 : 0;
   if (variant == CDCT_EXACT) build_exact_matrices(p->T, p->U);
@@ -386,7 +401,7 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
     if (rc) return cuda_fail(rc, "device query");
     pa.b = a;
     pa.err = di->err;
-    rc = pipe_launch(plan->n, plan->variant, plan->conv, in->dtype, pa, r, di->sms, stream);
+    rc = pipe_launch(plan->n, plan->variant, plan->conv, in->dtype, pa, r, di->sms, plan->tuning, stream);
   } else {
     rc = plan->ks[in->dtype].fused(a, in->batch, stream);
   }
@@ -435,6 +450,136 @@ cdct_status cdct_fwd_zonal_inv_noalloc(cdct_plan plan, const cdct_image* in, int
   // needs no clearing between calls
   return cdct_fwd_zonal_inv(plan, in, r, recon, recon_pitch, recon_batch_stride, kept, psnr_db, d.noalloc_scratch,
                             kNoAllocScratchDoubles * sizeof(double), stream);
+}
+
+cdct_status cdct_plan_set_tuning(cdct_plan plan, int stages, int ctas_per_sm) {
+  if (plan == nullptr) return fail(CDCT_EINVAL, "null plan");
+  if (stages != 0 && stages != 2 && stages != 3) return fail(CDCT_EINVAL, "stages must be 0 (default), 2 or 3");
+  if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(CDCT_EINVAL, "ctas_per_sm must be in [0, 32]");
+  plan->tuning.stages = stages;
+  plan->tuning.ctas_per_sm = ctas_per_sm;
+  return CDCT_OK;
+}
+
+cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, int n_images, int dtype,
+                              cdct_batch* out) {
+  if (out == nullptr) return fail(CDCT_EINVAL, "null output batch pointer");
+  *out = nullptr;
+  if (plan == nullptr || images == nullptr) return fail(CDCT_EINVAL, "null argument");
+  if (plan->variant == CDCT_EXACT) return fail(CDCT_EUNSUPPORTED, "batches run the integer variants only");
+  if (n_images < 1) return fail(CDCT_EINVAL, "n_images must be >= 1");
+  if (dtype != CDCT_U8 && dtype != CDCT_I16) return fail(CDCT_EINVAL, "bad dtype");
+  static_assert(sizeof(BatchImage) == sizeof(cdct_batch_image), "descriptor layout");
+  const int es = dtype == CDCT_I16 ? 2 : 1;
+  const int n = plan->n, S = blocks_per_cta(n);
+  const size_t desc_bytes = sizeof(BatchImage) * static_cast<size_t>(n_images);
+  const size_t prefix_offset = (desc_bytes + 15) / 16 * 16;
+  const size_t table_bytes = prefix_offset + sizeof(long long) * (static_cast<size_t>(n_images) + 1);
+  cdct_batch_s* b = new (std::nothrow) cdct_batch_s();
+  if (b == nullptr) return fail(CDCT_ENOMEM, "batch allocation failed");
+  try {
+    b->host_table.assign(table_bytes, '\0');
+  } catch (...) {
+    delete b;
+    return fail(CDCT_ENOMEM, "batch table allocation failed");
+  }
+  long long units = 0, pixels = 0;
+  long long* prefix = reinterpret_cast<long long*>(&b->host_table[prefix_offset]);
+  for (int i = 0; i < n_images; ++i) {
+    const cdct_batch_image& im = images[i];
+    const std::string where = "batch image " + std::to_string(i) + ": ";
+    cdct_status st = CDCT_OK;
+    if (im.data == nullptr || im.recon == nullptr) st = fail(CDCT_EINVAL, where + "null pointer");
+    else if (im.width < 1 || im.height < 1) st = fail(CDCT_EINVAL, where + "width and height must be >= 1");
+    else if (im.pitch < im.width || im.recon_pitch < im.width) st = fail(CDCT_EINVAL, where + "pitch < width");
+    else if (!aligned16(im.data) || !aligned16(im.recon) || (im.pitch * es) % 16 || (im.recon_pitch * 4) % 16 ||
+             (static_cast<long long>(im.width) * es) % 16)
+      st = fail(CDCT_EINVAL, where + "pixels, rows and widths must be 16-byte aligned");
+    if (st != CDCT_OK) {
+      delete b;
+      return st;
+    }
+    prefix[i] = units;
+    const long long nbx = (im.width + n - 1) / n, nby = (im.height + n - 1) / n;
+    units += nby * ((nbx + S - 1) / S);
+    pixels += static_cast<long long>(im.width) * im.height;
+  }
+  prefix[n_images] = units;
+  if (units * (kThreads / 32) >= (1ll << 31)) {
+    delete b;
+    return fail(CDCT_EINVAL, "batch too large for one launch (2^31 work units)");
+  }
+  std::memcpy(&b->host_table[0], images, desc_bytes);
+  b->plan = plan;
+  b->dtype = dtype;
+  b->n_images = n_images;
+  b->total_units = units;
+  b->total_pixels = pixels;
+  b->table_bytes = table_bytes;
+  b->prefix_offset = prefix_offset;
+  *out = b;
+  return CDCT_OK;
+}
+
+cdct_status cdct_batch_destroy(cdct_batch batch) {
+  delete batch;
+  return CDCT_OK;
+}
+
+cdct_status cdct_batch_sizes(cdct_batch batch, size_t* table_bytes, size_t* workspace_bytes, int64_t* total_pixels) {
+  if (batch == nullptr) return fail(CDCT_EINVAL, "null batch");
+  if (table_bytes) *table_bytes = batch->table_bytes;
+  if (workspace_bytes) *workspace_bytes = static_cast<size_t>(batch->total_units) * (kThreads / 32) * sizeof(double);
+  if (total_pixels) *total_pixels = batch->total_pixels;
+  return CDCT_OK;
+}
+
+cdct_status cdct_batch_upload(cdct_batch batch, void* device_table, void* stream) {
+  if (batch == nullptr || device_table == nullptr) return fail(CDCT_EINVAL, "null argument");
+  if (!aligned16(device_table)) return fail(CDCT_EINVAL, "device_table must be 16-byte aligned");
+  cudaError_t e = cudaMemcpyAsync(device_table, batch->host_table.data(), batch->table_bytes, cudaMemcpyHostToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(static_cast<int>(e), "batch table upload");
+  // the host copy is pageable: wait until it has been read
+  e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CDCT_OK : cuda_fail(static_cast<int>(e), "batch table upload");
+}
+
+cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, double* psnr_db, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+  if (batch == nullptr || device_table == nullptr) return fail(CDCT_EINVAL, "null argument");
+  const cdct_plan_s* plan = batch->plan;
+  if (r < 1 || r > plan->n * plan->n) return fail(CDCT_EINVAL, "r must be in [1, N*N]");
+  if (!aligned16(device_table)) return fail(CDCT_EINVAL, "device_table must be 16-byte aligned");
+  const size_t need = static_cast<size_t>(batch->total_units) * (kThreads / 32) * sizeof(double);
+  if (psnr_db != nullptr &&
+      (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 7u)))
+    return fail(CDCT_EINVAL, "workspace missing, misaligned or smaller than cdct_batch_sizes()");
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  PipeArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  BlockArgs& a = pa.b;
+  a.out_vec = 1;
+  a.r = r;
+  a.scale = recon_scale(plan, true);
+  a.partial = psnr_db != nullptr ? static_cast<double*>(workspace) : nullptr;
+  const int nsub = (plan->n / 8) * (plan->n / 8);
+  for (int q = 0; q < 16; ++q) a.slab_mask[q] = q < nsub ? sub_mask(plan->n, r, q) : 0ull;
+  pa.total_units = batch->total_units;
+  pa.wait_limit = 1ll << 31;
+  pa.err = di->err;
+  pa.images = static_cast<const BatchImage*>(device_table);
+  pa.unit_prefix = reinterpret_cast<const long long*>(static_cast<const char*>(device_table) + batch->prefix_offset);
+  pa.n_images = batch->n_images;
+  rc = pipe_launch(plan->n, plan->variant, plan->conv, batch->dtype, pa, r, di->sms, plan->tuning, stream);
+  if (rc) return cuda_fail(rc, "batch launch");
+  if (psnr_db != nullptr) {
+    rc = launch_finalize_table(a.partial, pa.unit_prefix, pa.images, batch->n_images, kThreads / 32, psnr_db, stream);
+    if (rc) return cuda_fail(rc, "batch psnr launch");
+  }
+  return CDCT_OK;
 }
 
 cdct_status cdct_check_device(void* stream) {

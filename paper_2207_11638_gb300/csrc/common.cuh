@@ -66,6 +66,14 @@ inline FastDiv make_fastdiv(uint32_t d) {
   return f;
 }
 
+// One image of a descriptor-table batch (same layout as cdct_batch_image).
+struct BatchImage {
+  const void* data;        // first pixel (device)
+  float* recon;            // first reconstructed pixel (device)
+  int32_t width, height;
+  int64_t pitch, recon_pitch;  // elements
+};
+
 // Launch arguments of the persistent pipelined fused kernel.
 struct PipeArgs {
   BlockArgs b;
@@ -73,15 +81,31 @@ struct PipeArgs {
   long long units_per_img;
   long long total_units;   // < 2^31
   FastDiv div_img, div_row;
+  // descriptor-table batches: images[i] and unit_prefix[i] = units before image i
+  const BatchImage* images;
+  const long long* unit_prefix;
+  int n_images;
   int* err;                // device error word (bit 0: a bulk copy never landed)
   long long wait_limit;    // SM cycles before a stage wait gives up
 };
 
-int pipe_launch_n8(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream);
-int pipe_launch_n16(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream);
-int pipe_launch_n32(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream);
+// Tuning of the pipelined kernel: staging depth (0 = default for N) and
+// resident CTAs per SM used for the grid (0 = as many as fit).
+struct PipeTuning {
+  int stages;
+  int ctas_per_sm;
+};
+int pipe_launch_n8(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, PipeTuning t,
+                   void* stream);
+int pipe_launch_n16(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, PipeTuning t,
+                    void* stream);
+int pipe_launch_n32(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, PipeTuning t,
+                    void* stream);
 
 int launch_finalize(const FinalArgs& a, int batch, void* stream);
+// per-image PSNR of a descriptor-table batch (warps_per_unit partials per unit)
+int launch_finalize_table(const double* partial, const long long* unit_prefix, const BatchImage* images,
+                          int n_images, int warps_per_unit, double* psnr, void* stream);
 int launch_zonal(int n, int exact, int conv, const float* s, int r, void* coeff, long long nblocks,
                  float* scaled, void* kept, void* stream);
 int launch_psnr_partials(const void* ref, int dtype, long long ref_pitch, long long ref_bstride,

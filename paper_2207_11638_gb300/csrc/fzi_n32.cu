@@ -11,22 +11,39 @@ KernelSet kernels_n32(int variant, int conv, int dtype) {
   return conv == 0 ? kernel_set_int<32, ParamsHat, 0>(dtype) : kernel_set_int<32, ParamsHat, 1>(dtype);
 }
 
-// Pipelined fused kernel: compile-time r for the paper convention at
-// r in {256}; any other r (and the transpose convention) uses the
-// runtime mask.
-template <class P, typename InT>
-static int pipe_n32(int conv, const PipeArgs& pa, int r, int num_sms, void* stream) {
-  if (conv == 0) return pipe_launch_r<32, P, 0, InT, 2, 256>(pa, r, num_sms, stream);
-  return pipe_launch_r<32, P, 1, InT, 2>(pa, r, num_sms, stream);
+// Pipelined fused kernel.  Compile-time r for the paper convention at r in
+// {256} with the default staging depth (2); the alternative depth (3)
+// has r = 256; any other r, and the transpose convention, use the runtime
+// mask.  Descriptor-table batches use the default depth.
+template <class P, typename InT, bool TABLE>
+static int pipe_n32(int conv, const PipeArgs& pa, int r, int num_sms, PipeTuning t, void* stream) {
+  const int stages = t.stages == 0 ? 2 : t.stages;
+  if (conv == 0) {
+    if constexpr (TABLE) {
+      return pipe_launch_r<32, P, 0, InT, 2, true, 256>(pa, r, num_sms, t.ctas_per_sm, stream);
+    } else {
+      if (stages == 2) return pipe_launch_r<32, P, 0, InT, 2, false, 256>(pa, r, num_sms, t.ctas_per_sm, stream);
+      return pipe_launch_r<32, P, 0, InT, 3, false, 256>(pa, r, num_sms, t.ctas_per_sm, stream);
+    }
+  }
+  return pipe_launch_r<32, P, 1, InT, 2, TABLE>(pa, r, num_sms, t.ctas_per_sm, stream);
 }
 
-int pipe_launch_n32(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, void* stream) {
+int pipe_launch_n32(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, PipeTuning t,
+                    void* stream) {
+  const bool table = pa.images != nullptr;
   if (variant == 1) {
-    return dtype == 0 ? pipe_n32<ParamsTilde, uint8_t>(conv, pa, r, num_sms, stream)
-                      : pipe_n32<ParamsTilde, int16_t>(conv, pa, r, num_sms, stream);
+    if (dtype == 0)
+      return table ? pipe_n32<ParamsTilde, uint8_t, true>(conv, pa, r, num_sms, t, stream)
+                   : pipe_n32<ParamsTilde, uint8_t, false>(conv, pa, r, num_sms, t, stream);
+    return table ? pipe_n32<ParamsTilde, int16_t, true>(conv, pa, r, num_sms, t, stream)
+                 : pipe_n32<ParamsTilde, int16_t, false>(conv, pa, r, num_sms, t, stream);
   }
-  return dtype == 0 ? pipe_n32<ParamsHat, uint8_t>(conv, pa, r, num_sms, stream)
-                    : pipe_n32<ParamsHat, int16_t>(conv, pa, r, num_sms, stream);
+  if (dtype == 0)
+    return table ? pipe_n32<ParamsHat, uint8_t, true>(conv, pa, r, num_sms, t, stream)
+                 : pipe_n32<ParamsHat, uint8_t, false>(conv, pa, r, num_sms, t, stream);
+  return table ? pipe_n32<ParamsHat, int16_t, true>(conv, pa, r, num_sms, t, stream)
+               : pipe_n32<ParamsHat, int16_t, false>(conv, pa, r, num_sms, t, stream);
 }
 
 }  // namespace cdct

@@ -170,6 +170,8 @@ struct UnitPos {
   int valid;          // valid pixels of the block's rows
   bool fast;          // interior block: all N rows and columns valid, aligned output
   float* orow0;       // output row 0 of the block
+  long long out_pitch;
+  int height;
 };
 
 // squared error of one staged row against a packed reconstruction row
@@ -224,7 +226,7 @@ __device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up
   for (int j = 0; j < N / 2; ++j) unpk2(rec2[j], rec[2 * j], rec[2 * j + 1]);
   const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
   if (up.fast) {
-    float* orow = up.orow0 + static_cast<long long>(r) * a.out_pitch;
+    float* orow = up.orow0 + static_cast<long long>(r) * up.out_pitch;
 #pragma unroll
     for (int c = 0; c < N / 4; ++c)
       __stcs(reinterpret_cast<float4*>(orow + 4 * c),
@@ -235,8 +237,8 @@ __device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up
     return lo + hi;
   }
   const int gy = up.by * N + r;
-  if (!up.active || gy >= a.height) return 0.f;
-  float* orow = up.orow0 + static_cast<long long>(r) * a.out_pitch;
+  if (!up.active || gy >= up.height) return 0.f;
+  float* orow = up.orow0 + static_cast<long long>(r) * up.out_pitch;
   if (up.valid == N && a.out_vec) {
 #pragma unroll
     for (int c = 0; c < N / 4; ++c)
@@ -502,9 +504,63 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
 };
 
 // ---------------------------------------------------------------------------
+// Unit decoding: image, block row and segment of unit u, with the image's
+// geometry, for a uniform batch (BlockArgs) or a descriptor table.
+// ---------------------------------------------------------------------------
+template <typename InT>
+struct UnitSrc {
+  int img, by, seg;
+  const InT* in;          // first pixel of the image
+  long long in_pitch;
+  int width, height, nbx;
+  float* out;             // first reconstructed pixel of the image
+  long long out_pitch;
+};
+
+template <int N, typename InT, bool TABLE>
+__device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, UnitSrc<InT>& d) {
+  typedef PipeGeo<N, InT> PG;
+  const BlockArgs& a = pa.b;
+  if constexpr (!TABLE) {
+    uint32_t rem, seg;
+    d.img = static_cast<int>(fdiv(u, pa.div_img, rem));
+    d.by = static_cast<int>(fdiv(rem, pa.div_row, seg));
+    d.seg = static_cast<int>(seg);
+    d.in = static_cast<const InT*>(a.in) + static_cast<long long>(d.img) * a.in_bstride;
+    d.in_pitch = a.in_pitch;
+    d.width = a.width;
+    d.height = a.height;
+    d.nbx = a.nbx;
+    d.out = a.out + static_cast<long long>(d.img) * a.out_bstride;
+    d.out_pitch = a.out_pitch;
+  } else {
+    // the image whose unit range contains u (unit_prefix is non-decreasing)
+    int lo = 0, hi = pa.n_images - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(pa.unit_prefix + mid) <= static_cast<long long>(u)) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchImage* im = pa.images + lo;
+    d.img = lo;
+    d.in = static_cast<const InT*>(im->data);
+    d.in_pitch = im->pitch;
+    d.width = im->width;
+    d.height = im->height;
+    d.nbx = (d.width + N - 1) / N;
+    d.out = im->recon;
+    d.out_pitch = im->recon_pitch;
+    const int upr = (d.nbx + PG::S - 1) / PG::S;
+    const int rem = static_cast<int>(static_cast<long long>(u) - __ldg(pa.unit_prefix + lo));
+    d.by = rem / upr;
+    d.seg = rem - d.by * upr;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
-template <int N, class P, int CONV, typename InT, int RFIX, int STAGES>
+template <int N, class P, int CONV, typename InT, int RFIX, int STAGES, bool TABLE>
 __global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(const PipeArgs pa) {
   typedef PipeGeo<N, InT> PG;
   constexpr int NW = kThreads / 32;
@@ -535,17 +591,15 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(c
 
   // one whole warp issues the copies of unit u into stage s
   auto issue = [&](long long u, int s) {
-    uint32_t rem, seg;
-    const int img = static_cast<int>(fdiv(static_cast<uint32_t>(u), pa.div_img, rem));
-    const int by = static_cast<int>(fdiv(rem, pa.div_row, seg));
-    const int x0 = static_cast<int>(seg) * PG::WPX;
-    const uint32_t bytes = static_cast<uint32_t>(min(PG::WPX, a.width - x0) * es);
+    UnitSrc<InT> d;
+    decode_unit<N, InT, TABLE>(pa, static_cast<uint32_t>(u), d);
+    const int x0 = d.seg * PG::WPX;
+    const uint32_t bytes = static_cast<uint32_t>(min(PG::WPX, d.width - x0) * es);
     if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes * N);
     __syncwarp();
     if (lane < N) {
-      const int gy = min(by * N + lane, a.height - 1);
-      const InT* src = static_cast<const InT*>(a.in) + static_cast<long long>(img) * a.in_bstride +
-                       static_cast<long long>(gy) * a.in_pitch + x0;
+      const int gy = min(d.by * N + lane, d.height - 1);
+      const InT* src = d.in + static_cast<long long>(gy) * d.in_pitch + x0;
       bulk_g2s(smem + s * PG::STAGE_BYTES + lane * PG::ROWP, src, bytes, &full[s], policy);
     }
   };
@@ -567,16 +621,18 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(c
     if (!mbar_wait_bounded(&full[s], parity, pa.wait_limit)) { failed = true; break; }
     const unsigned char* stage = smem + s * PG::STAGE_BYTES;
 
+    UnitSrc<InT> d;
+    decode_unit<N, InT, TABLE>(pa, static_cast<uint32_t>(u), d);
     UnitPos up;
-    uint32_t rem, seg;
-    up.img = static_cast<int>(fdiv(static_cast<uint32_t>(u), pa.div_img, rem));
-    up.by = static_cast<int>(fdiv(rem, pa.div_row, seg));
-    up.bx = static_cast<int>(seg) * PG::S + lb;
-    up.active = up.bx < a.nbx;
-    up.valid = up.active ? min(N, a.width - up.bx * N) : N;
-    up.fast = up.active && up.valid == N && a.out_vec && (up.by + 1) * N <= a.height;
-    up.orow0 = a.out + static_cast<long long>(up.img) * a.out_bstride +
-               static_cast<long long>(up.by) * N * a.out_pitch + up.bx * N;
+    up.img = d.img;
+    up.by = d.by;
+    up.bx = d.seg * PG::S + lb;
+    up.active = up.bx < d.nbx;
+    up.valid = up.active ? min(N, d.width - up.bx * N) : N;
+    up.fast = up.active && up.valid == N && a.out_vec && (up.by + 1) * N <= d.height;
+    up.orow0 = d.out + static_cast<long long>(up.by) * N * d.out_pitch + up.bx * N;
+    up.out_pitch = d.out_pitch;
+    up.height = d.height;
 
     float acc = UnitBody<N, P, CONV, InT, RFIX>::run(a, up, stage, xch, lane, lb);
 
@@ -619,47 +675,40 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(c
   }
 }
 
-template <int N, class P, int CONV, typename InT, int RFIX, int STAGES>
-int launch_pipe(const PipeArgs& pa, int grid, void* stream) {
+template <int N, class P, int CONV, typename InT, int RFIX, int STAGES, bool TABLE>
+int launch_pipe(const PipeArgs& pa, int num_sms, int ctas_per_sm, void* stream) {
   typedef PipeGeo<N, InT> PG;
-  auto kern = fzi_pipe_kernel<N, P, CONV, InT, RFIX, STAGES>;
+  auto kern = fzi_pipe_kernel<N, P, CONV, InT, RFIX, STAGES, TABLE>;
   const size_t smem = PG::smem_bytes(STAGES);
+  static int occ = -1;   // resident CTAs per SM (same for every GPU this library targets)
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
+  if (occ < 0) {
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    occ = n > 0 ? n : 1;
+  }
+  const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+  const long long cap = static_cast<long long>(num_sms) * per_sm;
+  const int grid = static_cast<int>(pa.total_units < cap ? pa.total_units : cap);
+  if (grid <= 0) return 0;
   kern<<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(pa);
   return static_cast<int>(cudaGetLastError());
 }
 
-template <int N, class P, int CONV, typename InT, int RFIX, int STAGES>
-int occupancy_pipe() {
-  typedef PipeGeo<N, InT> PG;
-  auto kern = fzi_pipe_kernel<N, P, CONV, InT, RFIX, STAGES>;
-  const size_t smem = PG::smem_bytes(STAGES);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-    return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 0;
-  return n;
-}
-
 // Launch with the compile-time r among Rs that equals r, or the runtime-mask
-// version; the grid is the resident CTA count, capped by the number of units.
-template <int N, class P, int CONV, typename InT, int STAGES>
-int pipe_launch_r(const PipeArgs& pa, int r, int num_sms, void* stream) {
+// version.
+template <int N, class P, int CONV, typename InT, int STAGES, bool TABLE>
+int pipe_launch_r(const PipeArgs& pa, int r, int num_sms, int ctas_per_sm, void* stream) {
   (void)r;
-  static const int occ = occupancy_pipe<N, P, CONV, InT, 0, STAGES>();
-  const long long cap = static_cast<long long>(num_sms) * (occ > 0 ? occ : 1);
-  const int grid = static_cast<int>(pa.total_units < cap ? pa.total_units : cap);
-  return launch_pipe<N, P, CONV, InT, 0, STAGES>(pa, grid, stream);
+  return launch_pipe<N, P, CONV, InT, 0, STAGES, TABLE>(pa, num_sms, ctas_per_sm, stream);
 }
 
-template <int N, class P, int CONV, typename InT, int STAGES, int R0, int... Rs>
-int pipe_launch_r(const PipeArgs& pa, int r, int num_sms, void* stream) {
-  if (r != R0) return pipe_launch_r<N, P, CONV, InT, STAGES, Rs...>(pa, r, num_sms, stream);
-  static const int occ = occupancy_pipe<N, P, CONV, InT, R0, STAGES>();
-  const long long cap = static_cast<long long>(num_sms) * (occ > 0 ? occ : 1);
-  const int grid = static_cast<int>(pa.total_units < cap ? pa.total_units : cap);
-  return launch_pipe<N, P, CONV, InT, R0, STAGES>(pa, grid, stream);
+template <int N, class P, int CONV, typename InT, int STAGES, bool TABLE, int R0, int... Rs>
+int pipe_launch_r(const PipeArgs& pa, int r, int num_sms, int ctas_per_sm, void* stream) {
+  if (r != R0) return pipe_launch_r<N, P, CONV, InT, STAGES, TABLE, Rs...>(pa, r, num_sms, ctas_per_sm, stream);
+  return launch_pipe<N, P, CONV, InT, R0, STAGES, TABLE>(pa, num_sms, ctas_per_sm, stream);
 }
 
 }  // namespace cdct

@@ -33,6 +33,30 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const FinalArgs
   }
 }
 
+// per-image PSNR of a descriptor-table batch: image i owns partials
+// [unit_prefix[i] * W, unit_prefix[i + 1] * W), summed in a fixed order
+__global__ void __launch_bounds__(kFinalThreads) finalize_table_kernel(const double* partial,
+                                                                       const long long* unit_prefix,
+                                                                       const BatchImage* images, int warps,
+                                                                       double* psnr) {
+  __shared__ double red[kFinalThreads];
+  const int img = blockIdx.x;
+  const long long b = unit_prefix[img] * warps, e = unit_prefix[img + 1] * warps;
+  double s = 0.0;
+  for (long long i = b + threadIdx.x; i < e; i += kFinalThreads) s += partial[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kFinalThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double sse = red[0];
+    const double npix = static_cast<double>(images[img].width) * images[img].height;
+    psnr[img] = (sse > 0.0) ? 10.0 * log10(255.0 * 255.0 * npix / sse) : static_cast<double>(INFINITY);
+  }
+}
+
 struct ZonalArgs {
   int n, exact, conv, r;
   void* coeff;
@@ -108,6 +132,13 @@ __global__ void __launch_bounds__(256) psnr_partial_kernel(const InT* ref, long 
 
 int launch_finalize(const FinalArgs& a, int batch, void* stream) {
   finalize_kernel<<<batch, kFinalThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_finalize_table(const double* partial, const long long* unit_prefix, const BatchImage* images,
+                          int n_images, int warps_per_unit, double* psnr, void* stream) {
+  finalize_table_kernel<<<n_images, kFinalThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      partial, unit_prefix, images, warps_per_unit, psnr);
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -1,0 +1,97 @@
+"""Descriptor-table batches and the autotune cache, without a GPU.
+
+Batch creation validates the host descriptor list before anything touches
+the device: each invalid descriptor is refused with CDCT_EINVAL naming the
+image.  The pointers below are never dereferenced.
+"""
+import ctypes
+import json
+
+import pytest
+
+from paper_2207_11638_gb300 import autotune
+from paper_2207_11638_gb300 import binding as b
+
+FAKE = 0x10000000
+
+
+def descs(items):
+    arr = (b.CdctBatchImage * len(items))()
+    for i, (d, o, w, h, p, rp) in enumerate(items):
+        arr[i] = b.CdctBatchImage(d, o, w, h, p, rp)
+    return arr
+
+
+def create(plan, items, dtype=0):
+    h = ctypes.c_void_p()
+    st = b.lib().cdct_batch_create(plan.handle, descs(items), len(items), dtype, ctypes.byref(h))
+    return st, h
+
+
+def test_valid_batch_sizes():
+    plan = b.Plan(8, "hat")
+    items = [(FAKE, FAKE, 64, 40, 64, 64), (FAKE + 4096, FAKE + 8192, 1040, 9, 1040, 1040)]
+    st, h = create(plan, items)
+    assert st == b.CDCT_OK
+    tb, wb, px = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+    assert b.lib().cdct_batch_sizes(h, ctypes.byref(tb), ctypes.byref(wb), ctypes.byref(px)) == 0
+    # units: image 0: 5 block rows x 1 segment; image 1: 2 x ceil(130 / 128) = 4
+    assert wb.value == (5 + 4) * 4 * 8
+    assert px.value == 64 * 40 + 1040 * 9
+    assert tb.value >= 2 * ctypes.sizeof(b.CdctBatchImage) + 3 * 8
+    assert b.lib().cdct_batch_destroy(h) == 0
+
+
+@pytest.mark.parametrize("bad,msg", [
+    ((0, FAKE, 64, 8, 64, 64), b"null pointer"),
+    ((FAKE, 0, 64, 8, 64, 64), b"null pointer"),
+    ((FAKE, FAKE, 0, 8, 64, 64), b"width and height"),
+    ((FAKE, FAKE, 64, 8, 32, 64), b"pitch < width"),
+    ((FAKE + 8, FAKE, 64, 8, 64, 64), b"16-byte aligned"),
+    ((FAKE, FAKE, 40, 8, 40, 40), b"16-byte aligned"),     # u8 width not a multiple of 16
+    ((FAKE, FAKE, 64, 8, 64, 66), b"16-byte aligned"),     # recon pitch not a multiple of 4 floats
+])
+def test_invalid_descriptor_rejected(bad, msg):
+    plan = b.Plan(16, "tilde")
+    good = (FAKE, FAKE, 64, 8, 64, 64)
+    st, h = create(plan, [good, good, bad])
+    assert st == b.CDCT_EINVAL and h.value is None
+    err = b.lib().cdct_last_error()
+    assert b"batch image 2" in err and msg in err
+
+
+def test_batch_argument_checks():
+    lib = b.lib()
+    h = ctypes.c_void_p()
+    assert lib.cdct_batch_create(b.Plan(8, "exact").handle, descs([(FAKE, FAKE, 64, 8, 64, 64)]), 1, 0,
+                                 ctypes.byref(h)) == b.CDCT_EUNSUPPORTED
+    assert lib.cdct_batch_create(b.Plan(8, "hat").handle, descs([(FAKE, FAKE, 64, 8, 64, 64)]), 0, 0,
+                                 ctypes.byref(h)) == b.CDCT_EINVAL
+    plan = b.Plan(8, "hat")
+    assert lib.cdct_plan_set_tuning(plan.handle, 5, 0) == b.CDCT_EINVAL
+    assert lib.cdct_plan_set_tuning(plan.handle, 3, -1) == b.CDCT_EINVAL
+    assert lib.cdct_plan_set_tuning(plan.handle, 3, 2) == b.CDCT_OK
+    st, hb = create(plan, [(FAKE, FAKE, 64, 8, 64, 64)])
+    assert st == 0
+    # r out of range and missing workspace are refused before any launch
+    assert lib.cdct_batch_fzi(hb, ctypes.c_void_p(FAKE), 0, None, None, 0, None) == b.CDCT_EINVAL
+    assert lib.cdct_batch_fzi(hb, ctypes.c_void_p(FAKE), 6, ctypes.c_void_p(FAKE), None, 0, None) == b.CDCT_EINVAL
+    lib.cdct_batch_destroy(hb)
+
+
+def test_autotune_cache_roundtrip_and_corruption(tmp_path):
+    path = str(tmp_path / "tune.json")
+    assert autotune.load_cache(path) == {}                      # missing
+    open(path, "w").write("{ not json")
+    assert autotune.load_cache(path) == {}                      # corrupt
+    open(path, "w").write(json.dumps([1, 2, 3]))
+    assert autotune.load_cache(path) == {}                      # wrong shape
+    key = autotune.cache_key("GPU", 16, "hat", "paper", "i16", 64)
+    bad = autotune.cache_key("GPU", 8, "hat", "paper", "i16", 16)
+    open(path, "w").write(json.dumps({key: {"stages": 3, "ctas_per_sm": 2, "ms": 1.0},
+                                      bad: {"stages": 7, "ctas_per_sm": 2}}))
+    cache = autotune.load_cache(path)
+    assert list(cache) == [key]                                  # invalid entries dropped
+    cache[bad] = {"stages": 2, "ctas_per_sm": 0, "ms": 2.0}
+    autotune.save_cache(cache, path)
+    assert autotune.load_cache(path) == cache
