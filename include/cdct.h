@@ -141,8 +141,9 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
                                void* stream);
 
 /* Pipeline tuning of a plan (the autotuner sets it): staging depth of the
- * fused kernel's input ring (0 = default for N, or 2, 3) and resident CTAs
- * per SM used for its persistent grid (0 = as many as fit).  Changes the
+ * fused kernel's input ring (0 = default for N, or 1, 2, 3; N = 8 runs 1 as
+ * 2; N = 16 and 32 at depth 1 are built for four resident CTAs per SM) and
+ * resident CTAs per SM used for its persistent grid (0 = as many as fit).  Changes the
  * schedule only, never the results.  Not to be called while another thread
  * uses the plan. */
 cdct_status cdct_plan_set_tuning(cdct_plan plan, int stages, int ctas_per_sm);

@@ -18,7 +18,7 @@ DEFAULT_CACHE = os.environ.get(
     "CDCT_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cdct", "autotune.json"))
 
 # (stages, ctas_per_sm): 0 = the kernel's default / as many CTAs as fit
-CANDIDATES = ((0, 0), (2, 0), (3, 0), (0, 2), (0, 3))
+CANDIDATES = ((0, 0), (1, 0), (2, 0), (3, 0), (0, 2), (0, 3))
 
 
 def cache_key(gpu: str, n: int, variant: str, conv: str, dtype: str, r: int) -> str:
@@ -36,7 +36,7 @@ def load_cache(path: str = DEFAULT_CACHE) -> dict:
     good = {}
     for k, v in data.items():
         if (isinstance(k, str) and isinstance(v, dict) and isinstance(v.get("stages"), int)
-                and isinstance(v.get("ctas_per_sm"), int) and v["stages"] in (0, 2, 3)
+                and isinstance(v.get("ctas_per_sm"), int) and v["stages"] in (0, 1, 2, 3)
                 and 0 <= v["ctas_per_sm"] <= 32):
             good[k] = v
     return good

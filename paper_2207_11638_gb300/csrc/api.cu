@@ -454,7 +454,7 @@ cdct_status cdct_fwd_zonal_inv_noalloc(cdct_plan plan, const cdct_image* in, int
 
 cdct_status cdct_plan_set_tuning(cdct_plan plan, int stages, int ctas_per_sm) {
   if (plan == nullptr) return fail(CDCT_EINVAL, "null plan");
-  if (stages != 0 && stages != 2 && stages != 3) return fail(CDCT_EINVAL, "stages must be 0 (default), 2 or 3");
+  if (stages < 0 || stages > 3) return fail(CDCT_EINVAL, "stages must be 0 (default), 1, 2 or 3");
   if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(CDCT_EINVAL, "ctas_per_sm must be in [0, 32]");
   plan->tuning.stages = stages;
   plan->tuning.ctas_per_sm = ctas_per_sm;

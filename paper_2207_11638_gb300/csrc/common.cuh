@@ -159,5 +159,16 @@ __host__ __device__ constexpr unsigned long long sub_mask(int n, int r, int q) {
       if (zigzag_pos(n, sub_row_of(n, q, i), sub_col_of(n, q, k)) < r) m |= 1ull << (k * 8 + i);
   return m;
 }
+// bits kept in at least one / in every sub-block of an N-point block
+__host__ __device__ constexpr unsigned long long sub_mask_any(int n, int r) {
+  unsigned long long m = 0;
+  for (int q = 0; q < (n / 8) * (n / 8); ++q) m |= sub_mask(n, r, q);
+  return m;
+}
+__host__ __device__ constexpr unsigned long long sub_mask_all(int n, int r) {
+  unsigned long long m = ~0ull;
+  for (int q = 0; q < (n / 8) * (n / 8); ++q) m &= sub_mask(n, r, q);
+  return m;
+}
 
 }  // namespace cdct

@@ -12,8 +12,8 @@ KernelSet kernels_n32(int variant, int conv, int dtype) {
 }
 
 // Pipelined fused kernel.  Compile-time r for the paper convention at r in
-// {256} with the default staging depth (2); the alternative depth (3)
-// has r = 256; any other r, and the transpose convention, use the runtime
+// {256} with the default staging depth (2); the alternative depths (1: four
+// resident CTAs per SM, 3) have r = 256; any other r, and the transpose convention, use the runtime
 // mask.  Descriptor-table batches use the default depth.
 template <class P, typename InT, bool TABLE>
 static int pipe_n32(int conv, const PipeArgs& pa, int r, int num_sms, PipeTuning t, void* stream) {
@@ -22,6 +22,7 @@ static int pipe_n32(int conv, const PipeArgs& pa, int r, int num_sms, PipeTuning
     if constexpr (TABLE) {
       return pipe_launch_r<32, P, 0, InT, 2, true, 256>(pa, r, num_sms, t.ctas_per_sm, stream);
     } else {
+      if (stages == 1) return pipe_launch_r<32, P, 0, InT, 1, false, 256>(pa, r, num_sms, t.ctas_per_sm, stream);
       if (stages == 2) return pipe_launch_r<32, P, 0, InT, 2, false, 256>(pa, r, num_sms, t.ctas_per_sm, stream);
       return pipe_launch_r<32, P, 0, InT, 3, false, 256>(pa, r, num_sms, t.ctas_per_sm, stream);
     }

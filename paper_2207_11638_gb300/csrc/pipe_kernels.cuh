@@ -64,9 +64,11 @@ struct PipeGeo {
   }
 };
 
-// resident CTAs per SM the register allocation is sized for
-template <int N>
-struct PipeOcc { static constexpr int value = (N == 8) ? 4 : 3; };
+// resident CTAs per SM the register allocation is sized for (N = 16 / 32
+// with a one-stage ring fit four CTAs in shared memory, so they are built
+// for four)
+template <int N, int STAGES>
+struct PipeOcc { static constexpr int value = (N == 8 || STAGES == 1) ? 4 : 3; };
 
 // Read row r (N pixels) of block lb from a staged unit with 128-bit shared
 // loads.  `valid` = number of valid pixels of this block's rows (N unless
@@ -118,12 +120,17 @@ __device__ __forceinline__ void ld_v4(const int* p, int* v) {
 // ---------------------------------------------------------------------------
 // The 8 x 8 core: forward rows / columns, zonal mask, kept coefficients,
 // inverse columns / rows.  v[i][j] holds row i on entry and on exit.  E is the
-// compile-time extent (rows / columns >= E are never kept).  With CT_MASK
-// (N = 8 and a compile-time r) the mask itself is a constant.
+// compile-time extent (rows / columns >= E are never kept).  With a
+// compile-time r (RFIX > 0) the bits that every sub-block keeps and the bits
+// that no sub-block keeps are constants; only the rest are selected with the
+// runtime mask m of this thread's sub-block q (for N = 8 none are left).  The
+// constant zeros also prune the butterflies that consume them.
 // ---------------------------------------------------------------------------
-template <int N, class P, int CONV, int E, bool CT_MASK, int RFIX>
+template <int N, class P, int CONV, int E, int RFIX>
 __device__ __forceinline__ void core8(int (&v)[8][8], unsigned long long m, int32_t* kept, int q) {
   typedef Ops<8, P, CONV> O;
+  constexpr unsigned long long ANY = RFIX > 0 ? sub_mask_any(N, RFIX) : ~0ull;
+  constexpr unsigned long long ALL = RFIX > 0 ? sub_mask_all(N, RFIX) : 0ull;
 #pragma unroll
   for (int i = 0; i < 8; ++i) O::fwd_row(v[i]);
   rows_to_cols<8>(nullptr, 0, 0, v);            // v[k][i]: column k
@@ -138,19 +145,23 @@ __device__ __forceinline__ void core8(int (&v)[8][8], unsigned long long m, int3
       for (int i = 0; i < 8; ++i) v[k][i] = 0;
     }
   }
-  const unsigned long long mk = CT_MASK ? sub_mask(8, RFIX > 0 ? RFIX : 64, 0) : m;
 #pragma unroll
   for (int k = 0; k < E; ++k)
 #pragma unroll
-    for (int i = 0; i < E; ++i)
-      if (!((mk >> (k * 8 + i)) & 1ull)) v[k][i] = 0;
+    for (int i = 0; i < E; ++i) {
+      const int bit = k * 8 + i;
+      if (!((ANY >> bit) & 1ull)) v[k][i] = 0;
+      else if (!((ALL >> bit) & 1ull) && !((m >> bit) & 1ull)) v[k][i] = 0;
+    }
   if (kept != nullptr) {
 #pragma unroll
     for (int k = 0; k < E; ++k)
 #pragma unroll
-      for (int i = 0; i < E; ++i)
-        if ((mk >> (k * 8 + i)) & 1ull)
+      for (int i = 0; i < E; ++i) {
+        const int bit = k * 8 + i;
+        if (((ANY >> bit) & 1ull) && (((ALL >> bit) & 1ull) || ((m >> bit) & 1ull)))
           kept[zigzag_pos(N, sub_row_of(N, q, i), sub_col_of(N, q, k))] = v[k][i] >> O::FWD_SHIFT;
+      }
   }
 #pragma unroll
   for (int k = 0; k < 8; ++k)
@@ -278,7 +289,7 @@ struct UnitBody<8, P, CONV, InT, RFIX> {
     int v[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) stage_read_row<8, InT>(stage, lb, i, up.valid, v[i]);
-    core8<8, P, CONV, E, (RFIX > 0), RFIX>(v, a.slab_mask[0], kept_ptr(a, up), 0);
+    core8<8, P, CONV, E, RFIX>(v, a.slab_mask[0], kept_ptr(a, up), 0);
     float acc = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc += store_row<8, InT>(a, up, stage, lb, i, v[i]);
@@ -341,7 +352,7 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
 #pragma unroll
         for (int ch = 0; ch < 2; ++ch) ld_v4(sb + off(0, i, ch), &v[i][4 * ch]);
       __syncwarp();
-      core8<16, P, CONV, E, false, RFIX>(v, a.slab_mask[s], kept_ptr(a, up), s);
+      core8<16, P, CONV, E, RFIX>(v, a.slab_mask[s], kept_ptr(a, up), s);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -449,7 +460,7 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
         pb -= step;
       }
       __syncwarp();
-      core8<32, P, CONV, E, false, RFIX>(v, a.slab_mask[q], kept_ptr(a, up), q);
+      core8<32, P, CONV, E, RFIX>(v, a.slab_mask[q], kept_ptr(a, up), q);
       int* qb = buf + l2(q, 0, 0);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
@@ -561,7 +572,7 @@ __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, Unit
 // The persistent kernel
 // ---------------------------------------------------------------------------
 template <int N, class P, int CONV, typename InT, int RFIX, int STAGES, bool TABLE>
-__global__ void __launch_bounds__(kThreads, PipeOcc<N>::value) fzi_pipe_kernel(const PipeArgs pa) {
+__global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_kernel(const PipeArgs pa) {
   typedef PipeGeo<N, InT> PG;
   constexpr int NW = kThreads / 32;
   const BlockArgs& a = pa.b;
