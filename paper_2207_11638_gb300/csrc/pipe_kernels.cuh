@@ -284,12 +284,13 @@ struct UnitBody;
 template <class P, int CONV, typename InT, int RFIX>
 struct UnitBody<8, P, CONV, InT, RFIX> {
   static constexpr int E = RFIX > 0 ? zonal_extent(8, RFIX) : 8;
+  static __device__ __forceinline__ int sub_block(int /*lane*/) { return 0; }
   static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
-                                              int* /*xch*/, int /*lane*/, int lb) {
+                                              int* /*xch*/, int /*lane*/, int lb, unsigned long long mask) {
     int v[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) stage_read_row<8, InT>(stage, lb, i, up.valid, v[i]);
-    core8<8, P, CONV, E, RFIX>(v, a.slab_mask[0], kept_ptr(a, up), 0);
+    core8<8, P, CONV, E, RFIX>(v, mask, kept_ptr(a, up), 0);
     float acc = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc += store_row<8, InT>(a, up, stage, lb, i, v[i]);
@@ -306,8 +307,9 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
   static constexpr int E = RFIX > 0 ? (zonal_extent(16, RFIX) + 1) / 2 : 8;
   // word offset of chunk (s, row, ch) within a block
   static constexpr int off(int s, int row, int ch) { return 4 * ((s * 8 + row) * 2 + ch); }
+  static __device__ __forceinline__ int sub_block(int lane) { return lane >> 3; }
   static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
-                                              int* xch, int lane, int lb) {
+                                              int* xch, int lane, int lb, unsigned long long mask) {
     const int p = lane >> 3, lbw = lane & 7;
     int* buf = xch + lbw * 65 * 4;
     int* rp = buf + 8 * p;              // row p of every sub-block
@@ -352,7 +354,7 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
 #pragma unroll
         for (int ch = 0; ch < 2; ++ch) ld_v4(sb + off(0, i, ch), &v[i][4 * ch]);
       __syncwarp();
-      core8<16, P, CONV, E, RFIX>(v, a.slab_mask[s], kept_ptr(a, up), s);
+      core8<16, P, CONV, E, RFIX>(v, mask, kept_ptr(a, up), s);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -406,8 +408,9 @@ template <class P, int CONV, typename InT, int RFIX>
 struct UnitBody<32, P, CONV, InT, RFIX> {
   static constexpr int E = RFIX > 0 ? (zonal_extent(32, RFIX) + 3) / 4 : 8;
   static constexpr int l2(int q, int row, int ch) { return 4 * (q * 17 + 2 * row + (row >> 2) + ch); }
+  static __device__ __forceinline__ int sub_block(int lane) { return lane & 15; }
   static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
-                                              int* xch, int lane, int lb) {
+                                              int* xch, int lane, int lb, unsigned long long mask) {
     const int p = lane & 15, lbw = lane >> 4;
     int* buf = xch + lbw * 288 * 4;
     {
@@ -460,7 +463,7 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
         pb -= step;
       }
       __syncwarp();
-      core8<32, P, CONV, E, RFIX>(v, a.slab_mask[q], kept_ptr(a, up), q);
+      core8<32, P, CONV, E, RFIX>(v, mask, kept_ptr(a, up), q);
       int* qb = buf + l2(q, 0, 0);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
@@ -622,6 +625,10 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     }
   }
 
+  // the thread's sub-block, hence its zonal mask, is the same in every unit
+  typedef UnitBody<N, P, CONV, InT, RFIX> Body;
+  const unsigned long long mask = a.slab_mask[Body::sub_block(lane)];
+
   bool failed = false;
   int it = 0;
   for (;; ++it) {
@@ -645,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     up.out_pitch = d.out_pitch;
     up.height = d.height;
 
-    float acc = UnitBody<N, P, CONV, InT, RFIX>::run(a, up, stage, xch, lane, lb);
+    float acc = Body::run(a, up, stage, xch, lane, lb, mask);
 
     if (a.partial != nullptr) {
 #pragma unroll
