@@ -204,6 +204,61 @@ cdct_status cdct_fwd_zonal_inv_noalloc(cdct_plan plan, const cdct_image* in, int
                                        int64_t recon_pitch, int64_t recon_batch_stride, void* kept,
                                        double* psnr_db, void* stream);
 
+/* ---- Exhaustive rate-distortion quadtree search (32 x 32 regions) -------
+ *
+ * The paper evaluates its 8-, 16- and 32-point transforms in a codec that
+ * picks the transform size per region (Sec. 6.2) but prints no search; this
+ * is the library's.  Every 32 x 32 region of the images (regions are tiled
+ * from the top-left corner; pixels beyond width x height are edge-replicated
+ * and excluded from the distortion) is evaluated, for each quantiser step q,
+ * with all 17 quadtrees: the whole region as one 32 x 32 block, or four
+ * 16 x 16 quadrants each kept or split into four 8 x 8 blocks.  Per block
+ * (paper convention of Sec. 5.1, T = T~_N or T^_N, U = N T^-1):
+ *   Y  = T A U; the scaled coefficients B = diag(s) Y diag(s)^-1 / N
+ *        (s_i = d_i^-1/2, d = diag(T T^T), Sec. 3.1) are quantised as
+ *        L = round(B / q) with the paper's round() (Sec. 3), decided exactly
+ *        in integers;
+ *   the decoder forms Y' = N q L c with c_ij = round(2^12 sqrt(d_i / d_j))
+ *        and Z' = U Y' T (the reconstruction times 2^12 N^2);
+ *   D  = sum over valid pixels of (2^12 N^2 A - Z')^2;
+ *   R  = 1 (coded-block flag) + 1 per zig-zag position up to the last
+ *        nonzero level + (2 floor(log2 |L|) + 2) per nonzero level;
+ *   J' = (32 / N)^4 D + lambda' R with lambda' = kappa q^2 2^44 and
+ *        kappa = kappa_num / 2^kappa_log2_den, i.e. J = SSE + kappa q^2 R
+ *        scaled by 2^24 32^4.
+ * A partition's cost adds one split-flag bit (lambda') per node that may
+ * split: the region, and each quadrant when the region is split.  The label
+ * minimises it; ties keep the larger transform.  Every quantity is an exact
+ * integer (128-bit costs), so labels are reproducible bit for bit.
+ *
+ * Labels: 0 = the whole region; 1 + m = split, where bit k of m (quadrant k
+ * in raster order: top-left, top-right, bottom-left, bottom-right) is set
+ * when that quadrant is split into 8 x 8 blocks. */
+typedef struct cdct_rd_s* cdct_rd;
+
+/* Host tables of a variant (CDCT_TILDE or CDCT_HAT): d and c for the three
+ * sizes.  Owns host memory only. */
+cdct_status cdct_rd_create(int variant, cdct_rd* out);
+cdct_status cdct_rd_destroy(cdct_rd rd);
+
+/* Host copy of the tables (for tests): 1440 int32 = d_i for N = 32, 16, 8
+ * (3 x 32, zero-padded), then c_ij row-major for N = 32, 16, 8. */
+cdct_status cdct_rd_tables(cdct_rd rd, int32_t* out);
+
+/* batch * ceil(width / 32) * ceil(height / 32); regions are numbered image
+ * by image, row-major within an image. */
+cdct_status cdct_rd_region_count(const cdct_image* in, int64_t* n_regions);
+
+/* One launch over every region for n_q (1..4) steps q (host array, each
+ * 1..4096).  kappa_num in 0..1024, kappa_log2_den in 0..44.
+ *   labels          device [n_q][n_regions] uint8
+ *   partition_cost  device [n_q][n_regions][17][2] uint64 (low, high words of
+ *                   each partition's 128-bit J', label order), or NULL.
+ * Pixels as for every entry point (CDCT_U8, or CDCT_I16 in [-255, 255]). */
+cdct_status cdct_rd_search(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q,
+                           int32_t kappa_num, int32_t kappa_log2_den, uint8_t* labels,
+                           uint64_t* partition_cost, void* stream);
+
 /* Synchronise `stream` and report whether a kernel of this library gave up
  * a bounded wait on the current device since the last check (the fused
  * kernel waits, with a time limit of about one second, for the bulk copies

@@ -125,10 +125,11 @@ def lambda_scaled(q: int, kappa_num: int, kappa_log2_den: int, frac_bits: int = 
 
 
 def block_cost(a: np.ndarray, variant: str, q: int, kappa_num: int, kappa_log2_den: int,
-               frac_bits: int = FRAC_BITS):
+               frac_bits: int = FRAC_BITS, valid=None):
     """(J'_block, D, R) of one N x N block a (N = a.shape[0]) on the common scale.
 
-    D = sum (2^F N^2 A - Z')^2 (unscaled), R = block_rate of the levels.
+    D = sum (2^F N^2 A - Z')^2 over the pixels where ``valid`` (default: all)
+    is true, unscaled; R = block_rate of the levels.
     """
     n = a.shape[0]
     t, u = _t_u(variant, n)
@@ -142,19 +143,23 @@ def block_cost(a: np.ndarray, variant: str, q: int, kappa_num: int, kappa_log2_d
     yd = np.array(yd, dtype=np.int64)
     z = u @ yd @ t                                       # Z' = U Y' T (exact in int64)
     e = (a.astype(np.int64) << frac_bits) * (n * n) - z
+    if valid is not None:
+        e = np.where(valid, e, 0)
     dist = sum(int(v) * int(v) for v in e.ravel())
     rate = block_rate(lv, n)
     scale = (REGION // n) ** 4
     return scale * dist + lambda_scaled(q, kappa_num, kappa_log2_den, frac_bits) * rate, dist, rate
 
 
-def region_block_costs(region: np.ndarray, variant: str, q: int, kappa_num: int, kappa_log2_den: int):
+def region_block_costs(region: np.ndarray, variant: str, q: int, kappa_num: int, kappa_log2_den: int,
+                       valid=None):
     """J' of the 21 blocks of a 32 x 32 region: {32: [J], 16: [4, raster], 8: [16, raster]}."""
     out = {}
     for n in SIZES:
         k = REGION // n
         out[n] = [block_cost(region[by * n:(by + 1) * n, bx * n:(bx + 1) * n], variant, q,
-                             kappa_num, kappa_log2_den)[0]
+                             kappa_num, kappa_log2_den,
+                             valid=None if valid is None else valid[by * n:(by + 1) * n, bx * n:(bx + 1) * n])[0]
                   for by in range(k) for bx in range(k)]
     return out
 
@@ -203,6 +208,33 @@ def rd_search(regions: np.ndarray, variant: str, qs, kappa_num: int = 1, kappa_l
         lam = lambda_scaled(q, kappa_num, kappa_log2_den)
         for r, reg in enumerate(regions):
             bc = region_block_costs(reg, variant, q, kappa_num, kappa_log2_den)
+            labels[qi, r] = dp_label(bc, lam)
+            costs[qi, r, :] = partition_costs(bc, lam)
+    return labels, costs
+
+
+def rd_search_image(imgs: np.ndarray, variant: str, qs, kappa_num: int = 1, kappa_log2_den: int = 2):
+    """rd_search over the 32 x 32 regions of images [B, H, W], tiled from the top-left corner:
+    pixels beyond H x W are edge-replicated and left out of the distortion.  Regions are
+    numbered image by image, row-major.  Returns labels [len(qs), R] and costs [len(qs), R, 17]."""
+    imgs = np.asarray(imgs)
+    _, h, w = imgs.shape
+    padded = pl.pad_replicate(imgs, REGION)
+    valid = np.zeros(padded.shape[1:], dtype=bool)
+    valid[:h, :w] = True
+    regions, masks = [], []
+    for img in padded:
+        for ty in range(padded.shape[1] // REGION):
+            for tx in range(padded.shape[2] // REGION):
+                sl = (slice(ty * REGION, (ty + 1) * REGION), slice(tx * REGION, (tx + 1) * REGION))
+                regions.append(img[sl])
+                masks.append(valid[sl])
+    labels = np.zeros((len(qs), len(regions)), dtype=np.uint8)
+    costs = np.empty((len(qs), len(regions), N_PARTITIONS), dtype=object)
+    for qi, q in enumerate(qs):
+        lam = lambda_scaled(q, kappa_num, kappa_log2_den)
+        for r, (reg, m) in enumerate(zip(regions, masks)):
+            bc = region_block_costs(reg, variant, q, kappa_num, kappa_log2_den, valid=None if m.all() else m)
             labels[qi, r] = dp_label(bc, lam)
             costs[qi, r, :] = partition_costs(bc, lam)
     return labels, costs

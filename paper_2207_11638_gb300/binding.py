@@ -26,6 +26,7 @@ EXPORTS = (
     "cdct_matrix", "cdct_last_error", "cdct_version", "cdct_check_device",
     "cdct_fwd_zonal_inv_noalloc", "cdct_plan_set_tuning", "cdct_batch_create", "cdct_batch_destroy",
     "cdct_batch_sizes", "cdct_batch_upload", "cdct_batch_fzi",
+    "cdct_rd_create", "cdct_rd_destroy", "cdct_rd_tables", "cdct_rd_region_count", "cdct_rd_search",
 )
 
 
@@ -86,6 +87,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cdct_batch_sizes": (ctypes.c_int, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(i64)]),
         "cdct_batch_upload": (ctypes.c_int, [vp, vp, vp]),
         "cdct_batch_fzi": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, sz, vp]),
+        "cdct_rd_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp)]),
+        "cdct_rd_destroy": (ctypes.c_int, [vp]),
+        "cdct_rd_tables": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
+        "cdct_rd_region_count": (ctypes.c_int, [img_p, ctypes.POINTER(i64)]),
+        "cdct_rd_search": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -373,3 +379,71 @@ def psnr(ref, recon, workspace=None, stream=None):
                           out.data_ptr(), workspace.data_ptr(),
                           workspace.numel() * workspace.element_size(), stream_handle(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Rate-distortion quadtree search (cdct_rd_*)
+# ---------------------------------------------------------------------------
+
+RD_PARTITIONS = 17
+RD_COST_SCALE = float(2 ** 24 * 32 ** 4)     # J' / RD_COST_SCALE = SSE + kappa q^2 R
+
+
+class RdSearch:
+    """Exhaustive RD quadtree search over the 32 x 32 regions of images.
+
+    ``variant``: "tilde" or "hat".  ``kappa`` = kappa_num / 2**kappa_log2_den
+    (lambda = kappa q^2; default 1/4)."""
+
+    def __init__(self, variant: str = "hat", kappa_num: int = 1, kappa_log2_den: int = 2):
+        self.variant, self.kappa_num, self.kappa_log2_den = variant, kappa_num, kappa_log2_den
+        h = ctypes.c_void_p()
+        check(lib().cdct_rd_create(VARIANTS[variant], ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _LIB is not None:
+            _LIB.cdct_rd_destroy(h)
+            self._h = None
+
+    def tables(self):
+        """(d {32, 16, 8: [N]}, c {32, 16, 8: [N][N]}) host tables, as lists."""
+        buf = (ctypes.c_int32 * 1440)()
+        check(lib().cdct_rd_tables(self._h, buf))
+        v = list(buf)
+        d = {n: v[k * 32:k * 32 + n] for k, n in enumerate((32, 16, 8))}
+        c, off = {}, 96
+        for n in (32, 16, 8):
+            c[n] = [v[off + i * n:off + (i + 1) * n] for i in range(n)]
+            off += n * n
+        return d, c
+
+    @staticmethod
+    def region_count(img) -> int:
+        d = image_desc(img)
+        n = ctypes.c_int64()
+        check(lib().cdct_rd_region_count(ctypes.byref(d), ctypes.byref(n)))
+        return n.value
+
+    def search(self, img, qs, costs: bool = False, stream=None):
+        """labels [len(qs), R] uint8 (device) and, with ``costs``, the 17 partition costs
+        [len(qs), R, 17] as (low, high) int64 word pairs [len(qs), R, 17, 2] (device)."""
+        torch = _torch()
+        d = image_desc(img)
+        n = self.region_count(img)
+        qs = [int(q) for q in qs]
+        qa = (ctypes.c_int32 * len(qs))(*qs)
+        labels = torch.empty((len(qs), n), dtype=torch.uint8, device=img.device)
+        pc = torch.empty((len(qs), n, RD_PARTITIONS, 2), dtype=torch.int64, device=img.device) if costs else None
+        check(lib().cdct_rd_search(self._h, ctypes.byref(d), qa, len(qs), self.kappa_num, self.kappa_log2_den,
+                                   labels.data_ptr(), pc.data_ptr() if costs else None, stream_handle(stream)))
+        return (labels, pc) if costs else labels
+
+
+def rd_cost_ints(pc_host) -> list:
+    """(low, high) uint64 word pairs (as int64) -> Python ints."""
+    import numpy as np
+    a = np.asarray(pc_host).astype(np.uint64)
+    lo, hi = a[..., 0], a[..., 1]
+    return [[[int(h) << 64 | int(l) for l, h in zip(lr, hr)] for lr, hr in zip(lq, hq)] for lq, hq in zip(lo, hi)]

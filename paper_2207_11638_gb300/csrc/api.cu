@@ -27,6 +27,11 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 
 struct cdct_batch_s;
 
+struct cdct_rd_s {
+  int variant;
+  int tables[3 * 32 + 32 * 32 + 16 * 16 + 8 * 8];   // host copy, passed to each launch by value
+};
+
 struct cdct_plan_s {
   int n, variant, conv;
   PipeTuning tuning;
@@ -596,6 +601,73 @@ cdct_status cdct_check_device(void* stream) {
   rc = static_cast<int>(cudaMemcpy(di->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
   if (rc) return cuda_fail(rc, "error word reset");
   return fail(CDCT_ETIMEOUT, "a kernel gave up waiting for its staged input (bounded wait expired)");
+}
+
+cdct_status cdct_rd_create(int variant, cdct_rd* out) {
+  if (out == nullptr) return fail(CDCT_EINVAL, "null output handle");
+  *out = nullptr;
+  if (variant != CDCT_TILDE && variant != CDCT_HAT)
+    return fail(CDCT_EINVAL, "the rate-distortion search needs CDCT_TILDE or CDCT_HAT");
+  cdct_rd_s* rd = new (std::nothrow) cdct_rd_s;
+  if (rd == nullptr) return fail(CDCT_ENOMEM, "out of host memory");
+  rd->variant = variant;
+  if (rd_table_words() != static_cast<int>(sizeof(rd->tables) / sizeof(int))) {
+    delete rd;
+    return fail(CDCT_EUNSUPPORTED, "internal table size mismatch");
+  }
+  rd_tables(variant, rd->tables);
+  *out = rd;
+  return CDCT_OK;
+}
+
+cdct_status cdct_rd_destroy(cdct_rd rd) {
+  delete rd;
+  return CDCT_OK;
+}
+
+cdct_status cdct_rd_tables(cdct_rd rd, int32_t* out) {
+  if (rd == nullptr || out == nullptr) return fail(CDCT_EINVAL, "null argument");
+  std::memcpy(out, rd->tables, sizeof(rd->tables));
+  return CDCT_OK;
+}
+
+cdct_status cdct_rd_region_count(const cdct_image* in, int64_t* n_regions) {
+  if (n_regions == nullptr) return fail(CDCT_EINVAL, "null output");
+  cdct_status st = check_image(in, "rd input");
+  if (st != CDCT_OK) return st;
+  *n_regions = static_cast<int64_t>(in->batch) * ((in->width + 31) / 32) * ((in->height + 31) / 32);
+  return CDCT_OK;
+}
+
+cdct_status cdct_rd_search(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q, int32_t kappa_num,
+                           int32_t kappa_log2_den, uint8_t* labels, uint64_t* partition_cost, void* stream) {
+  if (rd == nullptr) return fail(CDCT_EINVAL, "null rd handle");
+  int64_t n_regions = 0;
+  cdct_status st = cdct_rd_region_count(in, &n_regions);
+  if (st != CDCT_OK) return st;
+  if (q == nullptr || n_q < 1 || n_q > 4) return fail(CDCT_EINVAL, "n_q must be 1..4 with a host array q");
+  for (int k = 0; k < n_q; ++k)
+    if (q[k] < 1 || q[k] > 4096) return fail(CDCT_EINVAL, "quantiser steps must be in 1..4096");
+  if (kappa_num < 0 || kappa_num > 1024) return fail(CDCT_EINVAL, "kappa_num must be in 0..1024");
+  if (kappa_log2_den < 0 || kappa_log2_den > 44) return fail(CDCT_EINVAL, "kappa_log2_den must be in 0..44");
+  if (labels == nullptr) return fail(CDCT_EINVAL, "null labels pointer");
+  if (n_regions == 0) return CDCT_OK;
+  // lambda' = kappa_num q^2 2^(44 - kappa_log2_den) as a 128-bit integer
+  unsigned long long lo[4], hi[4];
+  for (int k = 0; k < n_q; ++k) {
+    const unsigned __int128 lam = static_cast<unsigned __int128>(static_cast<unsigned long long>(kappa_num) *
+                                                                 static_cast<unsigned long long>(q[k]) * q[k])
+                                  << (44 - kappa_log2_den);
+    lo[k] = static_cast<unsigned long long>(lam);
+    hi[k] = static_cast<unsigned long long>(lam >> 64);
+  }
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  rc = launch_rd(rd->variant, in->dtype, in->data, in->pitch, in->batch_stride, in->width, in->height, in->batch,
+                 rd->tables, q, n_q, lo, hi, labels, reinterpret_cast<unsigned long long*>(partition_cost), di->sms,
+                 stream);
+  return rc ? cuda_fail(rc, "rd launch") : CDCT_OK;
 }
 
 cdct_status cdct_matrix(cdct_plan plan, int which, double* out) {

@@ -128,47 +128,47 @@ struct InvK {
   static constexpr int kg = 2 / (P::g0 * P::g0 + P::g1 * P::g1);
 };
 
-template <class P>
-CDCT_DEV void st_2M2inv(int (&x)[8]) {  // 2 M_2^{-1} = diag(2 P_4^T, 2 A_1^{-1})
+template <class P, typename V>
+CDCT_DEV void st_2M2inv(V (&x)[8]) {  // 2 M_2^{-1} = diag(2 P_4^T, 2 A_1^{-1})
   typedef InvK<P> K;
-  int y0 = 2 * x[0], y1 = 2 * x[2], y2 = 2 * x[3], y3 = 2 * x[1];
-  int s4 = K::k03 * x[4], s5 = K::k12 * x[5], s6 = K::k12 * x[6], s7 = K::k03 * x[7];
-  int y4 = P::b0 * s4 + P::b3 * s7, y5 = P::b2 * s5 + P::b1 * s6;
-  int y6 = P::b1 * s5 - P::b2 * s6, y7 = P::b3 * s4 - P::b0 * s7;
+  V y0 = 2 * x[0], y1 = 2 * x[2], y2 = 2 * x[3], y3 = 2 * x[1];
+  V s4 = K::k03 * x[4], s5 = K::k12 * x[5], s6 = K::k12 * x[6], s7 = K::k03 * x[7];
+  V y4 = P::b0 * s4 + P::b3 * s7, y5 = P::b2 * s5 + P::b1 * s6;
+  V y6 = P::b1 * s5 - P::b2 * s6, y7 = P::b3 * s4 - P::b0 * s7;
   x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3; x[4] = y4; x[5] = y5; x[6] = y6; x[7] = y7;
 }
 
-template <class P>
-CDCT_DEV void st_2M2inv_t(int (&x)[8]) {  // (2 M_2^{-1})^T = diag(2 P_4, diag(k) A_1)
+template <class P, typename V>
+CDCT_DEV void st_2M2inv_t(V (&x)[8]) {  // (2 M_2^{-1})^T = diag(2 P_4, diag(k) A_1)
   typedef InvK<P> K;
-  int y0 = 2 * x[0], y1 = 2 * x[3], y2 = 2 * x[1], y3 = 2 * x[2];
-  int y4 = K::k03 * (P::b0 * x[4] + P::b3 * x[7]);
-  int y5 = K::k12 * (P::b2 * x[5] + P::b1 * x[6]);
-  int y6 = K::k12 * (P::b1 * x[5] - P::b2 * x[6]);
-  int y7 = K::k03 * (P::b3 * x[4] - P::b0 * x[7]);
+  V y0 = 2 * x[0], y1 = 2 * x[3], y2 = 2 * x[1], y3 = 2 * x[2];
+  V y4 = K::k03 * (P::b0 * x[4] + P::b3 * x[7]);
+  V y5 = K::k12 * (P::b2 * x[5] + P::b1 * x[6]);
+  V y6 = K::k12 * (P::b1 * x[5] - P::b2 * x[6]);
+  V y7 = K::k03 * (P::b3 * x[4] - P::b0 * x[7]);
   x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3; x[4] = y4; x[5] = y5; x[6] = y6; x[7] = y7;
 }
 
-template <class P>
-CDCT_DEV void st_2M3inv(int (&x)[8]) {  // 2 M_3^{-1} = diag(2 C-tilde^{-1}, A_2) (symmetric)
+template <class P, typename V>
+CDCT_DEV void st_2M3inv(V (&x)[8]) {  // 2 M_3^{-1} = diag(2 C-tilde^{-1}, A_2) (symmetric)
   typedef InvK<P> K;
-  int y0 = x[0] + x[1], y1 = x[0] - x[1];
-  int y2 = K::kg * (P::g1 * x[3] - P::g0 * x[2]), y3 = K::kg * (P::g1 * x[2] + P::g0 * x[3]);
-  int y4 = x[4] + x[5], y5 = x[4] - x[5], y6 = x[7] - x[6], y7 = x[6] + x[7];
+  V y0 = x[0] + x[1], y1 = x[0] - x[1];
+  V y2 = K::kg * (P::g1 * x[3] - P::g0 * x[2]), y3 = K::kg * (P::g1 * x[2] + P::g0 * x[3]);
+  V y4 = x[4] + x[5], y5 = x[4] - x[5], y6 = x[7] - x[6], y7 = x[6] + x[7];
   x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3; x[4] = y4; x[5] = y5; x[6] = y6; x[7] = y7;
 }
 
-template <class P>
-CDCT_DEV void st_2M4inv(int (&x)[8]) {  // 2 M_4^{-1} = diag(B_4, 2 A_3^{-1})
-  int y0 = x[0] + x[3], y1 = x[1] + x[2], y2 = x[1] - x[2], y3 = x[0] - x[3];
-  int y4 = 2 * x[7], y5 = x[5] - x[6], y6 = x[5] + x[6], y7 = 2 * x[4];
+template <class P, typename V>
+CDCT_DEV void st_2M4inv(V (&x)[8]) {  // 2 M_4^{-1} = diag(B_4, 2 A_3^{-1})
+  V y0 = x[0] + x[3], y1 = x[1] + x[2], y2 = x[1] - x[2], y3 = x[0] - x[3];
+  V y4 = 2 * x[7], y5 = x[5] - x[6], y6 = x[5] + x[6], y7 = 2 * x[4];
   x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3; x[4] = y4; x[5] = y5; x[6] = y6; x[7] = y7;
 }
 
-template <class P>
-CDCT_DEV void st_2M4inv_t(int (&x)[8]) {  // (2 M_4^{-1})^T = diag(B_4, 2 A_3^{-T})
-  int y0 = x[0] + x[3], y1 = x[1] + x[2], y2 = x[1] - x[2], y3 = x[0] - x[3];
-  int y4 = 2 * x[7], y5 = x[5] + x[6], y6 = x[6] - x[5], y7 = 2 * x[4];
+template <class P, typename V>
+CDCT_DEV void st_2M4inv_t(V (&x)[8]) {  // (2 M_4^{-1})^T = diag(B_4, 2 A_3^{-T})
+  V y0 = x[0] + x[3], y1 = x[1] + x[2], y2 = x[1] - x[2], y3 = x[0] - x[3];
+  V y4 = 2 * x[7], y5 = x[5] + x[6], y6 = x[6] - x[5], y7 = 2 * x[4];
   x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3; x[4] = y4; x[5] = y5; x[6] = y6; x[7] = y7;
 }
 
@@ -185,22 +185,22 @@ CDCT_DEV void T8t_apply(T (&x)[8]) {  // x <- T_C^T x = B_8 M_4^T M_3 M_2^T M_1 
   st_P8t(x); st_M1(x); st_M2t<P>(x); st_M3<P>(x); st_M4t<P>(x); st_B8(x);
 }
 
-template <class P>
-CDCT_DEV void W8_apply(int (&x)[8]) {  // x <- 2 U_8 x = B_8 (2M_4^-1)(2M_3^-1)(2M_2^-1) M_1 P_8^T x
-  st_P8t(x); st_M1(x); st_2M2inv<P>(x); st_2M3inv<P>(x); st_2M4inv<P>(x); st_B8(x);
+template <class P, typename V>
+CDCT_DEV void W8_apply(V (&x)[8]) {  // x <- 2 U_8 x = B_8 (2M_4^-1)(2M_3^-1)(2M_2^-1) M_1 P_8^T x
+  st_P8t(x); st_M1(x); st_2M2inv<P, V>(x); st_2M3inv<P, V>(x); st_2M4inv<P, V>(x); st_B8(x);
 }
 
-template <class P>
-CDCT_DEV void W8t_apply(int (&x)[8]) {  // x <- 2 U_8^T x = P_8 M_1 (2M_2^-1)^T (2M_3^-1) (2M_4^-1)^T B_8 x
-  st_B8(x); st_2M4inv_t<P>(x); st_2M3inv<P>(x); st_2M2inv_t<P>(x); st_M1(x); st_P8(x);
+template <class P, typename V>
+CDCT_DEV void W8t_apply(V (&x)[8]) {  // x <- 2 U_8^T x = P_8 M_1 (2M_2^-1)^T (2M_3^-1) (2M_4^-1)^T B_8 x
+  st_B8(x); st_2M4inv_t<P, V>(x); st_2M3inv<P, V>(x); st_2M2inv_t<P, V>(x); st_M1(x); st_P8(x);
 }
 
 // ---------------------------------------------------------------------------
 // JAM recursion (Sec. 6): M^add_N = [[I, I-bar], [I-bar, -I]] (symmetric),
 // M^per_N interleaves the halves (row 2k <- upper k, row 2k+1 <- lower k).
 // ---------------------------------------------------------------------------
-template <int N>
-CDCT_DEV void madd(int (&x)[N], int (&lo)[N / 2], int (&hi)[N / 2]) {  // (lo; hi) = M^add x
+template <int N, typename V>
+CDCT_DEV void madd(V (&x)[N], V (&lo)[N / 2], V (&hi)[N / 2]) {  // (lo; hi) = M^add x
 #pragma unroll
   for (int k = 0; k < N / 2; ++k) {
     lo[k] = x[k] + x[N - 1 - k];
@@ -208,8 +208,8 @@ CDCT_DEV void madd(int (&x)[N], int (&lo)[N / 2], int (&hi)[N / 2]) {  // (lo; h
   }
 }
 
-template <int N>
-CDCT_DEV void madd_join(int (&lo)[N / 2], int (&hi)[N / 2], int (&x)[N]) {  // x = M^add (lo; hi)
+template <int N, typename V>
+CDCT_DEV void madd_join(V (&lo)[N / 2], V (&hi)[N / 2], V (&x)[N]) {  // x = M^add (lo; hi)
 #pragma unroll
   for (int k = 0; k < N / 2; ++k) {
     x[k] = lo[k] + hi[N / 2 - 1 - k];
@@ -217,14 +217,14 @@ CDCT_DEV void madd_join(int (&lo)[N / 2], int (&hi)[N / 2], int (&x)[N]) {  // x
   }
 }
 
-template <int N>
-CDCT_DEV void interleave(int (&lo)[N / 2], int (&hi)[N / 2], int (&x)[N]) {  // x = M^per (lo; hi)
+template <int N, typename V>
+CDCT_DEV void interleave(V (&lo)[N / 2], V (&hi)[N / 2], V (&x)[N]) {  // x = M^per (lo; hi)
 #pragma unroll
   for (int k = 0; k < N / 2; ++k) { x[2 * k] = lo[k]; x[2 * k + 1] = hi[k]; }
 }
 
-template <int N>
-CDCT_DEV void deinterleave(int (&x)[N], int (&lo)[N / 2], int (&hi)[N / 2]) {  // (lo; hi) = M^per^T x
+template <int N, typename V>
+CDCT_DEV void deinterleave(V (&x)[N], V (&lo)[N / 2], V (&hi)[N / 2]) {  // (lo; hi) = M^per^T x
 #pragma unroll
   for (int k = 0; k < N / 2; ++k) { lo[k] = x[2 * k]; hi[k] = x[2 * k + 1]; }
 }
@@ -232,32 +232,36 @@ CDCT_DEV void deinterleave(int (&x)[N], int (&lo)[N / 2], int (&hi)[N / 2]) {  /
 template <int N, class P>
 struct Jam {
   // x <- T_N x = M^per diag(T_{N/2}, T_{N/2}) M^add x
-  static CDCT_DEV void T(int (&x)[N]) {
-    int lo[N / 2], hi[N / 2];
+  template <typename V>
+  static CDCT_DEV void T(V (&x)[N]) {
+    V lo[N / 2], hi[N / 2];
     madd<N>(x, lo, hi);
     Jam<N / 2, P>::T(lo);
     Jam<N / 2, P>::T(hi);
     interleave<N>(lo, hi, x);
   }
   // x <- T_N^T x = M^add diag(T_{N/2}^T, T_{N/2}^T) M^per^T x
-  static CDCT_DEV void Tt(int (&x)[N]) {
-    int lo[N / 2], hi[N / 2];
+  template <typename V>
+  static CDCT_DEV void Tt(V (&x)[N]) {
+    V lo[N / 2], hi[N / 2];
     deinterleave<N>(x, lo, hi);
     Jam<N / 2, P>::Tt(lo);
     Jam<N / 2, P>::Tt(hi);
     madd_join<N>(lo, hi, x);
   }
   // x <- W_N x = M^add diag(W_{N/2}, W_{N/2}) M^per^T x   (W_N = 2 N T_N^{-1})
-  static CDCT_DEV void W(int (&x)[N]) {
-    int lo[N / 2], hi[N / 2];
+  template <typename V>
+  static CDCT_DEV void W(V (&x)[N]) {
+    V lo[N / 2], hi[N / 2];
     deinterleave<N>(x, lo, hi);
     Jam<N / 2, P>::W(lo);
     Jam<N / 2, P>::W(hi);
     madd_join<N>(lo, hi, x);
   }
   // x <- W_N^T x = M^per diag(W_{N/2}^T, W_{N/2}^T) M^add x
-  static CDCT_DEV void Wt(int (&x)[N]) {
-    int lo[N / 2], hi[N / 2];
+  template <typename V>
+  static CDCT_DEV void Wt(V (&x)[N]) {
+    V lo[N / 2], hi[N / 2];
     madd<N>(x, lo, hi);
     Jam<N / 2, P>::Wt(lo);
     Jam<N / 2, P>::Wt(hi);
@@ -267,10 +271,14 @@ struct Jam {
 
 template <class P>
 struct Jam<8, P> {
-  static CDCT_DEV void T(int (&x)[8]) { T8_apply<P>(x); }
-  static CDCT_DEV void Tt(int (&x)[8]) { T8t_apply<P>(x); }
-  static CDCT_DEV void W(int (&x)[8]) { W8_apply<P>(x); }
-  static CDCT_DEV void Wt(int (&x)[8]) { W8t_apply<P>(x); }
+  template <typename V>
+  static CDCT_DEV void T(V (&x)[8]) { T8_apply<P>(x); }
+  template <typename V>
+  static CDCT_DEV void Tt(V (&x)[8]) { T8t_apply<P>(x); }
+  template <typename V>
+  static CDCT_DEV void W(V (&x)[8]) { W8_apply<P>(x); }
+  template <typename V>
+  static CDCT_DEV void Wt(V (&x)[8]) { W8t_apply<P>(x); }
 };
 
 }  // namespace cdct

@@ -103,6 +103,14 @@ int pipe_launch_n32(int variant, int conv, int dtype, const PipeArgs& pa, int r,
                     void* stream);
 
 int launch_finalize(const FinalArgs& a, int batch, void* stream);
+
+// Rate-distortion quadtree search (rd.cu)
+int rd_table_words();
+void rd_tables(int variant, int* out);
+int launch_rd(int variant, int dtype, const void* in, long long pitch, long long bstride, int width, int height,
+              int batch, const int* host_tables, const int* q, int nq, const unsigned long long* lam_lo,
+              const unsigned long long* lam_hi, unsigned char* labels, unsigned long long* part_cost, int num_sms,
+              void* stream);
 // per-image PSNR of a descriptor-table batch (warps_per_unit partials per unit)
 int launch_finalize_table(const double* partial, const long long* unit_prefix, const BatchImage* images,
                           int n_images, int warps_per_unit, double* psnr, void* stream);
