@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run every transform with its default pipeline schedule")
-    ap.add_argument("--workload", choices=("frames", "uneven"), default="frames",
+    ap.add_argument("--workload", choices=("frames", "uneven", "rd"), default="frames",
                     help="frames: 64 1080p 4:2:0 residual frames (default); uneven: 4096 u8 images of "
-                         "log-uniform sizes in one persistent launch per pass, CUDA-graph replay")
+                         "log-uniform sizes in one persistent launch per pass, CUDA-graph replay; rd: "
+                         "exhaustive RD quadtree search over 200k 32x32 residual regions at q = 8, 16, 32")
+    ap.add_argument("--regions", type=int, default=200_000, help="rd workload: number of 32x32 regions")
     ap.add_argument("--images", type=int, default=4096, help="uneven workload: number of images")
     return ap.parse_args()
 
@@ -432,12 +434,98 @@ def run_uneven(args):
     return 0
 
 
+# Additions of the fast algorithm per N-point vector, T~ and T^ (Tables 2 and 4);
+# the integer inverse W = 2U has the same stage structure.
+ADDS = {"tilde": {8: 26, 16: 68, 32: 168}, "hat": {8: 22, 16: 60, 32: 152}}
+INT32_LANES_PER_SM = 128
+
+
+def rd_ops_per_region(variant, nq):
+    """Butterfly adds of one region: the three forward 2-D transforms in int32 and, per q, the three
+    inverse 2-D transforms in int64 (two int32 operations per add).  The quantiser, rate and
+    distortion arithmetic is not counted, so the ALU fraction is a lower bound."""
+    fwd = sum(2 * 32 * (32 // n) * ADDS[variant][n] for n in (8, 16, 32))
+    return fwd + nq * 2 * fwd
+
+
+def run_rd(args):
+    import torch
+    from paper_2207_11638_gb300 import binding as b
+    from paper_2207_11638_gb300 import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("the rd workload runs on one GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    qs = (8, 16, 32)
+    t0 = time.time()
+    regs_h = synth.residual_regions_32(args.regions, seed=4)
+    gen_s = time.time() - t0
+    regs_p = torch.from_numpy(regs_h).pin_memory()
+    regs = regs_p.to(dev)
+    search = b.RdSearch("hat")
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        search.search(regs, qs)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(args.steps):
+            labels = search.search(regs, qs)
+        e.record(stream)
+        torch.cuda.synchronize()
+    b.check_device()
+    ms = s.elapsed_time(e)
+    npix = args.regions * 1024
+    value = npix * args.steps / (ms / 1e3) / 1e9
+    # end to end: regions from pinned host memory in, labels out, every step
+    lab_h = torch.empty(labels.shape, dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        regs.copy_(regs_p, non_blocking=True)
+        lab_h.copy_(search.search(regs, qs), non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = npix * args.steps / (e0.elapsed_time(e1) / 1e3) / 1e9
+    clk = clocks.summary()
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = 152 * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
+    achieved = rd_ops_per_region("hat", len(qs)) * args.regions / (ms / args.steps / 1e3) / 1e12
+    counts = torch.bincount(labels[1].long(), minlength=17).tolist()
+    line = {
+        "metric": "Gpixel/s exhaustive RD quadtree search (17 partitions x 3 q)", "value": value,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64/u128",
+        "data": "synthetic",
+        "config": {"workload": f"{args.regions} int16 32x32 residual regions (differences of AR(1) 512x512 "
+                               "images, rho 0.95), T^ transforms 8/16/32, q in {8, 16, 32}, lambda = q^2/4",
+                   "regions": args.regions, "generation_s": round(gen_s, 1),
+                   "l2": "inputs 410 MB, larger than L2; no flush", "labels_q16": counts},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "rd_kernel",
+                     "ops_per_region": rd_ops_per_region("hat", len(qs)),
+                     "peak_kind": "152 SMs x 128 INT32 lanes x sampled SM clock; ops = butterfly adds only"},
+        "cpu_baseline": None,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": npix * 2,
+                "d2h_bytes_per_step": int(labels.numel())},
+        "gpu_launches": args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "rd":
+        return run_rd(args)
     return run_ours(args)
 
 

@@ -41,6 +41,7 @@ constexpr int kPitch = 33;                   // padded row pitch (words)
 struct RdSmem {
   int d[3][32];                              // d_i for N = 32, 16, 8
   int c32[32 * 32], c16[16 * 16], c8[8 * 8]; // dequantisation scales
+  float sd[3][32];                           // sqrt(d_j) (first guesses of the quantiser only)
   int a[kRdWarps][32 * kPitch];              // regions
   long long buf[kRdWarps][32 * kPitch];      // transposes
   u128 cost[kRdWarps][4][21];                // block costs per q: [0] 32, [1..4] 16, [5..20] 8
@@ -57,18 +58,17 @@ __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
 }
 
 // round(B / q) for B = y s_i / (n s_j), decided exactly (see the file comment).
-__device__ __forceinline__ int quant_level(int y, int di, int dj, int n, int q) {
-  const unsigned long long a = static_cast<unsigned long long>(y < 0 ? -static_cast<long long>(y) : y);
+// `unit` = n^2 q^2 d_i; `est` = sqrt(d_j) / (n q sqrt(d_i)) in float gives a
+// first guess within one of the answer, which the integer tests then settle.
+__device__ __forceinline__ int quant_level(int y, unsigned dj, unsigned long long unit, float est) {
+  const unsigned a = static_cast<unsigned>(y < 0 ? -y : y);
   if (a == 0) return 0;
-  const unsigned long long lhs = 4ull * a * a * static_cast<unsigned long long>(dj);
-  const unsigned long long unit = static_cast<unsigned long long>(n) * n * q * q * di;
-  // float estimate within one of the answer, then the exact correction
-  long long k = static_cast<long long>(floorf(static_cast<float>(a) * sqrtf(static_cast<float>(dj) / di) /
-                                               static_cast<float>(n * q) + 0.5f));
+  const unsigned long long lhs = (static_cast<unsigned long long>(a) * a) * (4ull * dj);
+  int k = __float2int_rd(fmaf(static_cast<float>(a), est, 0.5f));
   if (k < 0) k = 0;
-  while (static_cast<unsigned long long>(2 * k + 1) * (2 * k + 1) * unit <= lhs) ++k;
-  while (k > 0 && static_cast<unsigned long long>(2 * k - 1) * (2 * k - 1) * unit > lhs) --k;
-  return y < 0 ? -static_cast<int>(k) : static_cast<int>(k);
+  while (static_cast<unsigned long long>(2 * k + 1) * static_cast<unsigned>(2 * k + 1) * unit <= lhs) ++k;
+  while (k > 0 && static_cast<unsigned long long>(2 * k - 1) * static_cast<unsigned>(2 * k - 1) * unit > lhs) --k;
+  return y < 0 ? -k : k;
 }
 
 __device__ __forceinline__ int level_bits(int l) {
@@ -131,8 +131,12 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
   __syncwarp();
   const int i = lane % N;                   // block-local row of this lane's coefficients
   const int di = dd[i];
+  const float* sdj = sm.sd[N == 32 ? 0 : (N == 16 ? 1 : 2)];
   for (int qi = 0; qi < ka.nq; ++qi) {
     const int q = ka.q[qi];
+    const unsigned long long unit = static_cast<unsigned long long>(N * N) * static_cast<unsigned>(q * q) *
+                                    static_cast<unsigned>(di);
+    const float est_i = 1.0f / (static_cast<float>(N * q) * sdj[i]);
     int rate[S], last[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) { rate[s] = 0; last[s] = -1; }
@@ -140,12 +144,13 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const int j = c % N;
-      const int l = quant_level(y[c], di, dd[j], N, q);
+      const int l = quant_level(y[c], static_cast<unsigned>(dd[j]), unit, sdj[j] * est_i);
       if (l != 0) {
         rate[c / N] += level_bits(l);
         last[c / N] = max(last[c / N], zigzag_pos(N, i, j));
       }
-      buf[lane * kPitch + c] = static_cast<long long>(N * q) * l * cc[i * N + j];
+      // |N q L| < 2^23 and c < 2^16: one 32 x 32 -> 64-bit product
+      buf[lane * kPitch + c] = static_cast<long long>(N * q * l) * cc[i * N + j];
     }
     __syncwarp();
     // inverse, columns: (2U) Y'
@@ -186,7 +191,10 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
           const long long ref = static_cast<long long>(sa[lane * kPitch + c]) * (N * N) << kRdFrac;
           const long long e = ref - (x[k] >> 1);              // 2Z' is even: exact
           const unsigned long long ae = static_cast<unsigned long long>(e < 0 ? -e : e);
-          if (lane < vrows && c < vcols) dist[s] += static_cast<u128>(ae) * ae;
+          if (lane < vrows && c < vcols) {
+            if (ae >> 32) dist[s] += static_cast<u128>(ae) * ae;
+            else dist[s] += static_cast<unsigned long long>(static_cast<unsigned>(ae)) * static_cast<unsigned>(ae);
+          }
         }
       }
     }
@@ -217,7 +225,7 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
 }
 
 template <class P, typename InT>
-__global__ void __launch_bounds__(kRdThreads) rd_kernel(const RdKernelArgs ka) {
+__global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RdSmem& sm = *reinterpret_cast<RdSmem*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,6 +234,8 @@ __global__ void __launch_bounds__(kRdThreads) rd_kernel(const RdKernelArgs ka) {
     const int total = 3 * 32 + 32 * 32 + 16 * 16 + 8 * 8;
     int* dst = &sm.d[0][0];
     for (int t = threadIdx.x; t < total; t += kRdThreads) dst[t] = ka.tables[t];
+    for (int t = threadIdx.x; t < 3 * 32; t += kRdThreads)
+      sm.sd[t / 32][t % 32] = sqrtf(static_cast<float>(ka.tables[t]));
   }
   __syncthreads();
   int* sa = sm.a[warp];
