@@ -82,3 +82,46 @@ def stage_list(variant: str, n: int):
 def additive_complexity(variant: str, n: int) -> int:
     """Total additions of the fast algorithm for T_N (Tables 2 and 4)."""
     return sum(stage_adds(s) for s in stage_list(variant, n))
+
+
+# ---------------------------------------------------------------------------
+# SSIM (Sec. 5.1 compares reconstructions by PSNR and by the structural
+# similarity index of Wang et al. 2004).  The paper cites the index without
+# restating it; the standard form is used: an 11 x 11 circularly symmetric
+# Gaussian window (sigma = 1.5, unit sum), K1 = 0.01, K2 = 0.03, L = 255,
+# local statistics only where the window lies inside the image, and the mean
+# of the SSIM map.
+# ---------------------------------------------------------------------------
+
+SSIM_WIN, SSIM_SIGMA, SSIM_K1, SSIM_K2, SSIM_L = 11, 1.5, 0.01, 0.03, 255.0
+
+
+def ssim_window(size: int = SSIM_WIN, sigma: float = SSIM_SIGMA) -> np.ndarray:
+    """w(i, j) proportional to exp(-((i - c)^2 + (j - c)^2) / (2 sigma^2)), summing to one."""
+    r = np.arange(size, dtype=np.float64) - (size - 1) / 2.0
+    g = np.exp(-(r[:, None] ** 2 + r[None, :] ** 2) / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _window_filter(a: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """sum_{k,l} w[k, l] a[i + k, j + l] for every window lying inside a."""
+    from numpy.lib.stride_tricks import sliding_window_view
+    return np.einsum("ijkl,kl->ij", sliding_window_view(a, w.shape), w)
+
+
+def ssim_map(x: np.ndarray, y: np.ndarray, peak: float = SSIM_L) -> np.ndarray:
+    """Local SSIM = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2))."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    w = ssim_window()
+    mx_, my_ = _window_filter(x, w), _window_filter(y, w)
+    sxx = _window_filter(x * x, w) - mx_ * mx_
+    syy = _window_filter(y * y, w) - my_ * my_
+    sxy = _window_filter(x * y, w) - mx_ * my_
+    c1, c2 = (SSIM_K1 * peak) ** 2, (SSIM_K2 * peak) ** 2
+    return ((2 * mx_ * my_ + c1) * (2 * sxy + c2)) / ((mx_ * mx_ + my_ * my_ + c1) * (sxx + syy + c2))
+
+
+def ssim(x: np.ndarray, y: np.ndarray, peak: float = SSIM_L) -> float:
+    """Mean SSIM of one image pair (at least 11 x 11)."""
+    return float(np.mean(ssim_map(x, y, peak)))
