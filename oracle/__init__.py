@@ -20,7 +20,13 @@ fractions) or float64:
   transform, zig-zag zonal retention of r coefficients, inverse transform and
   PSNR, for the approximations and for the exact DCT.
 * ``metrics``   -- deviation from diagonality (Sec. 3.1), total error energy
-  and unified coding gain (Sec. 4.1), additive complexity (Tables 2 and 4).
+  and unified coding gain (Sec. 4.1), additive complexity (Tables 2 and 4),
+  and the SSIM index the experiment of Sec. 5.1 reports.
+* ``rd``        -- the exhaustive rate-distortion quadtree search over 32 x 32
+  regions (transform sizes 32 / 16 / 8, as in the codec of Sec. 6.2).
+* ``cnn``       -- the learned size selector that proposes the quadtree
+  instead: forward, backward, loss and Adam in float64 with the GPU's
+  bfloat16 rounding points.
 
 Parity status per function is stated in each function's docstring: every
 function is pinned by at least one ``-m "not gpu"`` test except the coding
