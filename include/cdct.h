@@ -259,6 +259,124 @@ cdct_status cdct_rd_search(cdct_rd rd, const cdct_image* in, const int32_t* q, i
                            int32_t kappa_num, int32_t kappa_log2_den, uint8_t* labels,
                            uint64_t* partition_cost, void* stream);
 
+/* cdct_rd_search restricted to the regions listed in region_index (device
+ * int64, numbers as for cdct_rd_search); their count is read on the device
+ * from *count (device int64, e.g. written by cdct_cnn_select), at most
+ * max_count (0..n_regions) entries are used, and numbers outside the image
+ * set are skipped.  Only the listed regions' labels (and costs) are
+ * written; the rest of `labels` is left as it was.  With cdct_cnn_select
+ * this is the selector's fallback: the exhaustive search re-decides the
+ * regions the network is unsure of. */
+cdct_status cdct_rd_search_subset(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q,
+                                  int32_t kappa_num, int32_t kappa_log2_den, const int64_t* region_index,
+                                  const int64_t* count, int64_t max_count, uint8_t* labels,
+                                  uint64_t* partition_cost, void* stream);
+
+/* Code every region with a given quadtree (labels device [n_q][n_regions],
+ * each < 17; a larger value is read as 0) and report, per step and region,
+ * with the definitions of cdct_rd_search:
+ *   cost  device [n_q][n_regions][2] uint64: J' of that partition (low, high)
+ *   dist  device [n_q][n_regions][2] uint64: its distortion on the J' scale,
+ *         sum over its blocks of (32 / N)^4 D = 2^24 32^4 SSE, or NULL
+ *   bits  device [n_q][n_regions] int32: its rate R including the split
+ *         flags, or NULL
+ * Only the transform sizes the partition uses are computed.  This is the
+ * encoder's final pass after a size decision, by the search or the network. */
+cdct_status cdct_rd_evaluate(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q, int32_t kappa_num,
+                             int32_t kappa_log2_den, const uint8_t* labels, uint64_t* cost, uint64_t* dist,
+                             int32_t* bits, void* stream);
+
+/* ---- Learned quadtree selector (a small CNN) ---------------------------
+ *
+ * The paper's codec experiment (Sec. 6.2) leaves the transform-size choice
+ * to the encoder; cdct_rd_search makes it by trying all 17 quadtrees.  This
+ * network proposes the quadtree instead, from the region's pixels and the
+ * quantiser slot; it is trained on the search's own labels (and, optionally,
+ * its partition costs), and the search stays available as fallback and judge.
+ * The network is the library's, not the paper's:
+ *   a0 = x / 64 (x the region's pixels, 32 x 32, edge-replicated as for
+ *        cdct_rd_search);
+ *   a_l = maxpool2x2(relu(conv3x3(a_{l-1}, W_l) + b_l)), l = 1, 2, 3, with
+ *        zero padding, channels 1 -> 16 -> 32 -> 32, sizes 32 -> 16 -> 8 -> 4;
+ *   h = a_3 flattened in (y, x, channel) order (512 values);  u = Wf1 h;
+ *   for quantiser slot k (0..3, a one-hot input):
+ *        g = relu(u + bf1 + Wq[:, k]),  logits = Wf2 g + bf2 (17 labels, the
+ *        label numbering of cdct_rd_search); the label is the first maximum.
+ * Precision: weights (W_l, Wf1, Wq, Wf2) are used as bfloat16 copies (round
+ * to nearest even) of float32 master weights; biases stay float32; every
+ * stored activation (a_l, g) is bfloat16; products accumulate in float32 on
+ * the tensor cores (mma.sync m16n8k16).
+ *
+ * Parameters: one float32 vector of CDCT_CNN_PARAMS values, in this order:
+ *   W1 [16][3][3][1]   b1 [16]   W2 [32][3][3][16]  b2 [32]
+ *   W3 [32][3][3][32]  b3 [32]   Wf1 [64][512]      Wq [64][4]   bf1 [64]
+ *   Wf2 [17][64]       bf2 [17]
+ * (W_l[o][dy][dx][i] multiplies a_{l-1}[y + dy - 1][x + dx - 1][i]).  The
+ * caller owns every buffer (device memory) and initialises the weights. */
+#define CDCT_CNN_PARAMS 48241
+#define CDCT_CNN_LABELS 17
+#define CDCT_CNN_SLOTS 4
+
+/* Bytes of the packed inference weights (a multiple of 256). */
+size_t cdct_cnn_packed_bytes(void);
+
+/* params (device, CDCT_CNN_PARAMS floats) -> packed (device,
+ * cdct_cnn_packed_bytes(), 16-byte aligned): the bfloat16 weights in the
+ * layouts the inference kernel reads.  Re-run after every weight update. */
+cdct_status cdct_cnn_pack(const float* params, void* packed, void* stream);
+
+/* Proposed labels of every 32 x 32 region of `in` (regions numbered as for
+ * cdct_rd_search) for n_slots (1..4) quantiser slots (host array, each
+ * 0..3).  One fused launch.  Outputs (device):
+ *   labels  [n_slots][n_regions] uint8 (required)
+ *   logits  [n_slots][n_regions][17] float, or NULL
+ *   margin  [n_slots][n_regions] float: best minus second-best logit (the
+ *           selector's confidence; 0 on ties), or NULL */
+cdct_status cdct_cnn_infer(const void* packed, const cdct_image* in, const int32_t* slots, int32_t n_slots,
+                           uint8_t* labels, float* logits, float* margin, void* stream);
+
+/* Regions the selector is unsure of: every region whose smallest margin
+ * over the n_slots slots (margin device [n_slots][n_regions], as written by
+ * cdct_cnn_infer) is below `threshold`.  Their numbers go to region_index
+ * (device int64, room for n_regions) in no particular order and their count
+ * to *count (device int64, reset by the call).  Feed both to
+ * cdct_rd_search_subset. */
+cdct_status cdct_cnn_select(const float* margin, int64_t n_regions, int32_t n_slots, float threshold,
+                            int64_t* region_index, int64_t* count, void* stream);
+
+/* Device workspace of cdct_cnn_grad for `batch` regions (batch a positive
+ * multiple of 64). */
+cdct_status cdct_cnn_workspace_size(int32_t batch, size_t* bytes);
+
+/* Loss and gradient of one batch, no update.
+ *   regions   device int16 [batch][32][32], pixels in [-255, 255]
+ *   slots     host [n_slots] (1..4 slots, each 0..3)
+ *   labels    device uint8 [n_slots][batch], each < 17 (targets)
+ *   partition_cost  device uint64 [n_slots][batch][17][2]: the 17
+ *             partition costs J' per sample as cdct_rd_search writes them,
+ *             or NULL (then mu is ignored); they give the normalised regret
+ *             c_j = (J_j - J_min) / J_min (evaluated in double precision)
+ *   grad      device float [CDCT_CNN_PARAMS] (overwritten)
+ *   loss      device float [1]: mean over the batch x n_slots samples of
+ *             -log p_label + mu sum_j p_j c_j, p = softmax(logits)
+ *   workspace device, cdct_cnn_workspace_size() bytes, 256-byte aligned.
+ * The forward pass repeats the inference arithmetic layer by layer; the
+ * backward pass rounds du, dh and the input gradients of conv3 and conv2 to
+ * bfloat16 before each product, treats every rounding as the identity, and
+ * sends a max pool's gradient to the first maximum of its window (raster
+ * order).  Weight gradients are reduced in a fixed order: the result is
+ * reproducible bit for bit. */
+cdct_status cdct_cnn_grad(const float* params, const int16_t* regions, int32_t batch, const int32_t* slots,
+                          int32_t n_slots, const uint8_t* labels, const uint64_t* partition_cost, float mu,
+                          float* grad, float* loss, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One Adam step (Kingma and Ba, 2015) in place on params, with state m, v
+ * (device, CDCT_CNN_PARAMS floats each, zero before step 1) and step >= 1:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   params -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+cdct_status cdct_cnn_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr,
+                          float beta1, float beta2, float eps, void* stream);
+
 /* Synchronise `stream` and report whether a kernel of this library gave up
  * a bounded wait on the current device since the last check (the fused
  * kernel waits, with a time limit of about one second, for the bulk copies

@@ -27,7 +27,10 @@ EXPORTS = (
     "cdct_fwd_zonal_inv_noalloc", "cdct_plan_set_tuning", "cdct_batch_create", "cdct_batch_destroy",
     "cdct_batch_sizes", "cdct_batch_upload", "cdct_batch_fzi",
     "cdct_rd_create", "cdct_rd_destroy", "cdct_rd_tables", "cdct_rd_region_count", "cdct_rd_search",
+    "cdct_cnn_packed_bytes", "cdct_cnn_pack", "cdct_cnn_infer", "cdct_cnn_workspace_size", "cdct_cnn_grad",
+    "cdct_cnn_adam", "cdct_rd_search_subset", "cdct_rd_evaluate", "cdct_cnn_select",
 )
+CNN_PARAMS, CNN_LABELS, CNN_SLOTS = 48241, 17, 4
 
 
 class CdctImage(ctypes.Structure):
@@ -92,6 +95,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cdct_rd_tables": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
         "cdct_rd_region_count": (ctypes.c_int, [img_p, ctypes.POINTER(i64)]),
         "cdct_rd_search": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp]),
+        "cdct_rd_search_subset": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i32), i32, i32, i32, vp, vp, i64, vp,
+                                                 vp, vp]),
+        "cdct_rd_evaluate": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp, vp, vp]),
+        "cdct_cnn_select": (ctypes.c_int, [vp, i64, i32, ctypes.c_float, vp, vp, vp]),
+        "cdct_cnn_packed_bytes": (sz, []),
+        "cdct_cnn_pack": (ctypes.c_int, [vp, vp, vp]),
+        "cdct_cnn_infer": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i32), i32, vp, vp, vp, vp]),
+        "cdct_cnn_workspace_size": (ctypes.c_int, [i32, ctypes.POINTER(sz)]),
+        "cdct_cnn_grad": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), i32, vp, vp, ctypes.c_float, vp, vp, vp,
+                                         sz, vp]),
+        "cdct_cnn_adam": (ctypes.c_int, [vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -440,6 +455,47 @@ class RdSearch:
                                    labels.data_ptr(), pc.data_ptr() if costs else None, stream_handle(stream)))
         return (labels, pc) if costs else labels
 
+    def search_subset(self, img, qs, region_index, count, labels, costs=None, stream=None):
+        """Re-decide the regions listed in region_index (device int64; *count of them,
+        a device int64) into ``labels`` [len(qs), R] in place (and ``costs`` if given)."""
+        d = image_desc(img)
+        n = self.region_count(img)
+        qs = [int(q) for q in qs]
+        qa = (ctypes.c_int32 * len(qs))(*qs)
+        check(lib().cdct_rd_search_subset(self._h, ctypes.byref(d), qa, len(qs), self.kappa_num, self.kappa_log2_den,
+                                          region_index.data_ptr(), count.data_ptr(), min(n, region_index.numel()),
+                                          labels.data_ptr(),
+                                          costs.data_ptr() if costs is not None else None, stream_handle(stream)))
+        return labels
+
+    def evaluate(self, img, qs, labels, stream=None):
+        """(cost [len(qs), R, 2], dist [len(qs), R, 2] as (low, high) int64 words, bits
+        [len(qs), R] int32) of coding every region with the labelled quadtree (device)."""
+        torch = _torch()
+        d = image_desc(img)
+        n = self.region_count(img)
+        qs = [int(q) for q in qs]
+        qa = (ctypes.c_int32 * len(qs))(*qs)
+        cost = torch.empty((len(qs), n, 2), dtype=torch.int64, device=img.device)
+        dist = torch.empty((len(qs), n, 2), dtype=torch.int64, device=img.device)
+        bits = torch.empty((len(qs), n), dtype=torch.int32, device=img.device)
+        check(lib().cdct_rd_evaluate(self._h, ctypes.byref(d), qa, len(qs), self.kappa_num, self.kappa_log2_den,
+                                     labels.contiguous().data_ptr(), cost.data_ptr(), dist.data_ptr(),
+                                     bits.data_ptr(), stream_handle(stream)))
+        return cost, dist, bits
+
+
+def cnn_select(margin, threshold: float, stream=None):
+    """(region_index [R] int64, count [1] int64) device tensors: the regions whose smallest
+    margin over the slots (margin [n_slots, R]) is below ``threshold``."""
+    torch = _torch()
+    ns, n = margin.shape
+    idx = torch.empty(max(n, 1), dtype=torch.int64, device=margin.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=margin.device)
+    check(lib().cdct_cnn_select(margin.contiguous().data_ptr(), n, ns, float(threshold), idx.data_ptr(),
+                                cnt.data_ptr(), stream_handle(stream)))
+    return idx, cnt
+
 
 def rd_cost_ints(pc_host) -> list:
     """(low, high) uint64 word pairs (as int64) -> Python ints."""
@@ -447,3 +503,86 @@ def rd_cost_ints(pc_host) -> list:
     a = np.asarray(pc_host).astype(np.uint64)
     lo, hi = a[..., 0], a[..., 1]
     return [[[int(h) << 64 | int(l) for l, h in zip(lr, hr)] for lr, hr in zip(lq, hq)] for lq, hq in zip(lo, hi)]
+
+
+class Cnn:
+    """Learned quadtree selector (include/cdct.h, cdct_cnn_*).
+
+    ``params``: device float32 tensor of CNN_PARAMS master weights, owned by
+    this object (updated in place by ``adam``); Adam state and the packed
+    inference weights live beside it.  ``slots`` index the quantiser steps the
+    network was trained for (0..3)."""
+
+    def __init__(self, params):
+        torch = _torch()
+        if params.dtype != torch.float32 or params.numel() != CNN_PARAMS or not params.is_cuda:
+            raise ValueError("params must be a CUDA float32 tensor of CNN_PARAMS values")
+        self.params = params.contiguous()
+        dev = self.params.device
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self.packed = torch.empty(lib().cdct_cnn_packed_bytes(), dtype=torch.uint8, device=dev)
+        self._ws = None
+        self.grad_buf = torch.empty_like(self.params)
+        self.loss_buf = torch.empty(1, dtype=torch.float32, device=dev)
+
+    def pack(self, stream=None):
+        check(lib().cdct_cnn_pack(self.params.data_ptr(), self.packed.data_ptr(), stream_handle(stream)))
+
+    def infer(self, img, slots, logits: bool = False, margin: bool = False, stream=None):
+        """labels [len(slots), R] uint8 (device); with ``logits`` / ``margin`` also
+        [len(slots), R, 17] and [len(slots), R] float32.  Uses the last ``pack``."""
+        torch = _torch()
+        d = image_desc(img)
+        n = RdSearch.region_count(img)
+        slots = [int(k) for k in slots]
+        sa = (ctypes.c_int32 * len(slots))(*slots)
+        lab = torch.empty((len(slots), n), dtype=torch.uint8, device=img.device)
+        lg = torch.empty((len(slots), n, CNN_LABELS), dtype=torch.float32, device=img.device) if logits else None
+        mg = torch.empty((len(slots), n), dtype=torch.float32, device=img.device) if margin else None
+        check(lib().cdct_cnn_infer(self.packed.data_ptr(), ctypes.byref(d), sa, len(slots), lab.data_ptr(),
+                                   lg.data_ptr() if logits else None, mg.data_ptr() if margin else None,
+                                   stream_handle(stream)))
+        out = [lab] + ([lg] if logits else []) + ([mg] if margin else [])
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def workspace(self, batch: int):
+        torch = _torch()
+        n = ctypes.c_size_t()
+        check(lib().cdct_cnn_workspace_size(int(batch), ctypes.byref(n)))
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = torch.empty(n.value, dtype=torch.uint8, device=self.params.device)
+        return self._ws
+
+    def grad(self, regions, slots, labels, costs=None, mu: float = 0.0, stream=None):
+        """(grad [CNN_PARAMS], loss [1]) device tensors for int16 regions [B, 32, 32]
+        (B a multiple of 64), labels [len(slots), B] uint8 and, for the regret term,
+        the search's partition costs [len(slots), B, 17, 2] (int64 words)."""
+        torch = _torch()
+        if regions.dtype != torch.int16 or regions.dim() != 3 or tuple(regions.shape[1:]) != (32, 32):
+            raise ValueError("regions must be int16 [B, 32, 32]")
+        regions = regions.contiguous()
+        labels = labels.contiguous()
+        B = regions.shape[0]
+        slots = [int(k) for k in slots]
+        sa = (ctypes.c_int32 * len(slots))(*slots)
+        ws = self.workspace(B)
+        if costs is not None:
+            costs = costs.contiguous()
+        check(lib().cdct_cnn_grad(self.params.data_ptr(), regions.data_ptr(), B, sa, len(slots), labels.data_ptr(),
+                                  costs.data_ptr() if costs is not None else None, float(mu),
+                                  self.grad_buf.data_ptr(), self.loss_buf.data_ptr(), ws.data_ptr(), ws.numel(),
+                                  stream_handle(stream)))
+        return self.grad_buf, self.loss_buf
+
+    def adam(self, grad, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+        self.step += 1
+        check(lib().cdct_cnn_adam(self.params.data_ptr(), grad.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                  self.step, float(lr), float(beta1), float(beta2), float(eps), stream_handle(stream)))
+
+    def train_step(self, regions, slots, labels, lr: float, costs=None, mu: float = 0.0, stream=None):
+        """Gradient + Adam update; returns the (device) loss of the batch before the update."""
+        g, loss = self.grad(regions, slots, labels, costs, mu, stream)
+        self.adam(g, lr, stream=stream)
+        return loss

@@ -10,6 +10,7 @@
 
 #include "../../include/cdct.h"
 #include "butterfly.cuh"
+#include "cnn.cuh"
 #include "common.cuh"
 
 using namespace cdct;
@@ -668,6 +669,172 @@ cdct_status cdct_rd_search(cdct_rd rd, const cdct_image* in, const int32_t* q, i
                  rd->tables, q, n_q, lo, hi, labels, reinterpret_cast<unsigned long long*>(partition_cost), di->sms,
                  stream);
   return rc ? cuda_fail(rc, "rd launch") : CDCT_OK;
+}
+
+namespace {
+// argument checks shared by the RD entry points; lambda' per step as 128-bit words
+cdct_status rd_common(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q, int32_t kappa_num,
+                      int32_t kappa_log2_den, int64_t* n_regions, unsigned long long* lo, unsigned long long* hi) {
+  if (rd == nullptr) return fail(CDCT_EINVAL, "null rd handle");
+  cdct_status st = cdct_rd_region_count(in, n_regions);
+  if (st != CDCT_OK) return st;
+  if (q == nullptr || n_q < 1 || n_q > 4) return fail(CDCT_EINVAL, "n_q must be 1..4 with a host array q");
+  for (int k = 0; k < n_q; ++k)
+    if (q[k] < 1 || q[k] > 4096) return fail(CDCT_EINVAL, "quantiser steps must be in 1..4096");
+  if (kappa_num < 0 || kappa_num > 1024) return fail(CDCT_EINVAL, "kappa_num must be in 0..1024");
+  if (kappa_log2_den < 0 || kappa_log2_den > 44) return fail(CDCT_EINVAL, "kappa_log2_den must be in 0..44");
+  for (int k = 0; k < n_q; ++k) {
+    const unsigned __int128 lam = static_cast<unsigned __int128>(static_cast<unsigned long long>(kappa_num) *
+                                                                 static_cast<unsigned long long>(q[k]) * q[k])
+                                  << (44 - kappa_log2_den);
+    lo[k] = static_cast<unsigned long long>(lam);
+    hi[k] = static_cast<unsigned long long>(lam >> 64);
+  }
+  return CDCT_OK;
+}
+}  // namespace
+
+cdct_status cdct_rd_search_subset(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q,
+                                  int32_t kappa_num, int32_t kappa_log2_den, const int64_t* region_index,
+                                  const int64_t* count, int64_t max_count, uint8_t* labels,
+                                  uint64_t* partition_cost, void* stream) {
+  int64_t n_regions = 0;
+  unsigned long long lo[4], hi[4];
+  cdct_status st = rd_common(rd, in, q, n_q, kappa_num, kappa_log2_den, &n_regions, lo, hi);
+  if (st != CDCT_OK) return st;
+  if (labels == nullptr || region_index == nullptr || count == nullptr)
+    return fail(CDCT_EINVAL, "null labels, region_index or count pointer");
+  if (max_count < 0 || max_count > n_regions) return fail(CDCT_EINVAL, "max_count must be in 0..n_regions");
+  if (max_count == 0) return CDCT_OK;
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  RdModeArgs m{};
+  m.mode = 1;
+  m.subset = reinterpret_cast<const long long*>(region_index);
+  m.subset_count = reinterpret_cast<const long long*>(count);
+  m.max_count = max_count;
+  rc = launch_rd(rd->variant, in->dtype, in->data, in->pitch, in->batch_stride, in->width, in->height, in->batch,
+                 rd->tables, q, n_q, lo, hi, labels, reinterpret_cast<unsigned long long*>(partition_cost), di->sms,
+                 stream, &m);
+  return rc ? cuda_fail(rc, "rd subset launch") : CDCT_OK;
+}
+
+cdct_status cdct_rd_evaluate(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q, int32_t kappa_num,
+                             int32_t kappa_log2_den, const uint8_t* labels, uint64_t* cost, uint64_t* dist,
+                             int32_t* bits, void* stream) {
+  int64_t n_regions = 0;
+  unsigned long long lo[4], hi[4];
+  cdct_status st = rd_common(rd, in, q, n_q, kappa_num, kappa_log2_den, &n_regions, lo, hi);
+  if (st != CDCT_OK) return st;
+  if (labels == nullptr || cost == nullptr) return fail(CDCT_EINVAL, "null labels or cost pointer");
+  if (n_regions == 0) return CDCT_OK;
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  RdModeArgs m{};
+  m.mode = 2;
+  m.in_labels = labels;
+  m.ev_cost = reinterpret_cast<unsigned long long*>(cost);
+  m.ev_dist = reinterpret_cast<unsigned long long*>(dist);
+  m.ev_bits = bits;
+  rc = launch_rd(rd->variant, in->dtype, in->data, in->pitch, in->batch_stride, in->width, in->height, in->batch,
+                 rd->tables, q, n_q, lo, hi, nullptr, nullptr, di->sms, stream, &m);
+  return rc ? cuda_fail(rc, "rd evaluate launch") : CDCT_OK;
+}
+
+cdct_status cdct_cnn_select(const float* margin, int64_t n_regions, int32_t n_slots, float threshold,
+                            int64_t* region_index, int64_t* count, void* stream) {
+  if (margin == nullptr || region_index == nullptr || count == nullptr) return fail(CDCT_EINVAL, "null pointer argument");
+  if (n_regions < 0) return fail(CDCT_EINVAL, "n_regions must be >= 0");
+  if (n_slots < 1 || n_slots > CDCT_CNN_SLOTS) return fail(CDCT_EINVAL, "n_slots must be 1..4");
+  if (std::isnan(threshold)) return fail(CDCT_EINVAL, "threshold is NaN");
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  rc = cnn_select_launch(margin, n_regions, n_slots, threshold, reinterpret_cast<long long*>(region_index),
+                         reinterpret_cast<long long*>(count), di->sms, stream);
+  return rc ? cuda_fail(rc, "cnn select launch") : CDCT_OK;
+}
+
+// ---- learned quadtree selector ----------------------------------------------
+
+size_t cdct_cnn_packed_bytes(void) { return cnn::kPackedBytes; }
+
+cdct_status cdct_cnn_pack(const float* params, void* packed, void* stream) {
+  if (params == nullptr || packed == nullptr) return fail(CDCT_EINVAL, "null params or packed pointer");
+  if (!aligned16(params) || !aligned16(packed)) return fail(CDCT_EINVAL, "params and packed must be 16-byte aligned");
+  const int rc = cnn_pack_launch(params, packed, stream);
+  return rc ? cuda_fail(rc, "cnn pack launch") : CDCT_OK;
+}
+
+namespace {
+cdct_status check_slots(const int32_t* slots, int32_t n_slots) {
+  if (slots == nullptr || n_slots < 1 || n_slots > CDCT_CNN_SLOTS)
+    return fail(CDCT_EINVAL, "n_slots must be 1..4 with a host array of slots");
+  for (int k = 0; k < n_slots; ++k)
+    if (slots[k] < 0 || slots[k] >= CDCT_CNN_SLOTS) return fail(CDCT_EINVAL, "quantiser slots must be in 0..3");
+  return CDCT_OK;
+}
+}  // namespace
+
+cdct_status cdct_cnn_infer(const void* packed, const cdct_image* in, const int32_t* slots, int32_t n_slots,
+                           uint8_t* labels, float* logits, float* margin, void* stream) {
+  if (packed == nullptr || !aligned16(packed)) return fail(CDCT_EINVAL, "packed weights: null or not 16-byte aligned");
+  int64_t n_regions = 0;
+  cdct_status st = cdct_rd_region_count(in, &n_regions);
+  if (st != CDCT_OK) return st;
+  st = check_slots(slots, n_slots);
+  if (st != CDCT_OK) return st;
+  if (labels == nullptr) return fail(CDCT_EINVAL, "null labels pointer");
+  if (n_regions == 0) return CDCT_OK;
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  int sl[CDCT_CNN_SLOTS];
+  for (int k = 0; k < n_slots; ++k) sl[k] = slots[k];
+  rc = cnn_infer_launch(packed, in->data, in->dtype, in->pitch, in->batch_stride, in->width, in->height, in->batch,
+                        sl, n_slots, labels, logits, margin, di->sms, stream);
+  return rc ? cuda_fail(rc, "cnn inference launch") : CDCT_OK;
+}
+
+cdct_status cdct_cnn_workspace_size(int32_t batch, size_t* bytes) {
+  if (bytes == nullptr) return fail(CDCT_EINVAL, "null bytes pointer");
+  if (batch < 64 || batch % 64 != 0) return fail(CDCT_EINVAL, "batch must be a positive multiple of 64");
+  *bytes = cnn_train_workspace(batch);
+  return CDCT_OK;
+}
+
+cdct_status cdct_cnn_grad(const float* params, const int16_t* regions, int32_t batch, const int32_t* slots,
+                          int32_t n_slots, const uint8_t* labels, const uint64_t* partition_cost, float mu,
+                          float* grad, float* loss, void* workspace, size_t workspace_bytes, void* stream) {
+  if (params == nullptr || regions == nullptr || labels == nullptr || grad == nullptr || loss == nullptr ||
+      workspace == nullptr)
+    return fail(CDCT_EINVAL, "null pointer argument");
+  if (batch < 64 || batch % 64 != 0) return fail(CDCT_EINVAL, "batch must be a positive multiple of 64");
+  cdct_status st = check_slots(slots, n_slots);
+  if (st != CDCT_OK) return st;
+  if (!(mu >= 0.f) || !std::isfinite(mu)) return fail(CDCT_EINVAL, "mu must be finite and >= 0");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return fail(CDCT_EINVAL, "workspace must be 256-byte aligned");
+  if (!aligned16(params) || !aligned16(grad)) return fail(CDCT_EINVAL, "params and grad must be 16-byte aligned");
+  if (workspace_bytes < cnn_train_workspace(batch)) return fail(CDCT_EINVAL, "workspace too small");
+  int sl[CDCT_CNN_SLOTS];
+  for (int k = 0; k < n_slots; ++k) sl[k] = slots[k];
+  const int rc = cnn_grad_launch(params, regions, batch, sl, n_slots, labels,
+                                 reinterpret_cast<const unsigned long long*>(partition_cost), mu, grad, loss, workspace,
+                                 stream);
+  return rc ? cuda_fail(rc, "cnn gradient launch") : CDCT_OK;
+}
+
+cdct_status cdct_cnn_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr, float beta1,
+                          float beta2, float eps, void* stream) {
+  if (params == nullptr || grad == nullptr || m == nullptr || v == nullptr) return fail(CDCT_EINVAL, "null pointer argument");
+  if (step < 1) return fail(CDCT_EINVAL, "step must be >= 1");
+  if (!(lr > 0.f) || !std::isfinite(lr) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+      !(eps > 0.f) || !std::isfinite(eps))
+    return fail(CDCT_EINVAL, "need lr > 0, 0 <= beta1, beta2 < 1 and eps > 0");
+  const int rc = cnn_adam_launch(params, grad, m, v, step, lr, beta1, beta2, eps, stream);
+  return rc ? cuda_fail(rc, "adam launch") : CDCT_OK;
 }
 
 cdct_status cdct_matrix(cdct_plan plan, int which, double* out) {

@@ -107,10 +107,22 @@ int launch_finalize(const FinalArgs& a, int batch, void* stream);
 // Rate-distortion quadtree search (rd.cu)
 int rd_table_words();
 void rd_tables(int variant, int* out);
+// mode 0: search every region; 1: search the listed regions (subset, device count);
+// 2: evaluate given labels (in_labels) -> ev_cost / ev_dist / ev_bits
+struct RdModeArgs {
+  int mode;
+  const long long* subset;
+  const long long* subset_count;
+  long long max_count;
+  const unsigned char* in_labels;
+  unsigned long long* ev_cost;
+  unsigned long long* ev_dist;
+  int* ev_bits;
+};
 int launch_rd(int variant, int dtype, const void* in, long long pitch, long long bstride, int width, int height,
               int batch, const int* host_tables, const int* q, int nq, const unsigned long long* lam_lo,
               const unsigned long long* lam_hi, unsigned char* labels, unsigned long long* part_cost, int num_sms,
-              void* stream);
+              void* stream, const RdModeArgs* mode = nullptr);
 // per-image PSNR of a descriptor-table batch (warps_per_unit partials per unit)
 int launch_finalize_table(const double* partial, const long long* unit_prefix, const BatchImage* images,
                           int n_images, int warps_per_unit, double* psnr, void* stream);

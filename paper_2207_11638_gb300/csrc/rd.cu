@@ -87,12 +87,31 @@ struct RdKernelArgs {
   unsigned char* labels;                     // [nq][n_regions]
   unsigned long long* part_cost;             // [nq][n_regions][17][2] or null
   int tables[3 * 32 + 32 * 32 + 16 * 16 + 8 * 8];   // d[3][32], c32, c16, c8 (by value)
+  // subset search (mode 1): region numbers and their count (device)
+  const long long* subset;
+  const long long* subset_count;
+  long long max_count;
+  // evaluation of given labels (mode 2)
+  const unsigned char* in_labels;            // [nq][n_regions]
+  unsigned long long* ev_cost;               // [nq][n_regions][2]: J' of the labelled partition
+  unsigned long long* ev_dist;               // [nq][n_regions][2]: its distortion on the J' scale, or null
+  int* ev_bits;                              // [nq][n_regions]: its rate in bits, or null
+};
+
+// Per-block distortion and rate, kept beside the costs when labels are evaluated.
+struct RdEvalSmem {
+  u128 dist[kRdWarps][4][21];
+  int bits[kRdWarps][4][21];
 };
 
 // One transform size for the region staged in sa; block costs into cost[qi][...].
+// `need`: bit qi set when step qi needs this size (all steps when searching);
+// `edist` / `ebits` (evaluation only, else null) receive each block's scaled
+// distortion and rate.
 template <int N, class P>
 __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm, const int* sa, long long* buf,
-                                        u128 (*cost)[21], int lane, int vrows, int vcols) {
+                                        u128 (*cost)[21], int lane, int vrows, int vcols, unsigned need,
+                                        u128 (*edist)[21], int (*ebits)[21]) {
   constexpr int S = 32 / N;
   int* b32 = reinterpret_cast<int*>(buf);
   const int* dd = sm.d[N == 32 ? 0 : (N == 16 ? 1 : 2)];
@@ -133,6 +152,7 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
   const int di = dd[i];
   const float* sdj = sm.sd[N == 32 ? 0 : (N == 16 ? 1 : 2)];
   for (int qi = 0; qi < ka.nq; ++qi) {
+    if (!((need >> qi) & 1u)) continue;      // warp-uniform
     const int q = ka.q[qi];
     const unsigned long long unit = static_cast<unsigned long long>(N * N) * static_cast<unsigned>(q * q) *
                                     static_cast<unsigned>(di);
@@ -218,16 +238,26 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
       for (int s = 0; s < S; ++s) {
         const int bits = 1 + (last[s] + 1) + rate[s];
         cost[qi][cost_base(N) + br * S + s] = dist[s] * kScale + lam * static_cast<unsigned>(bits);
+        if (edist != nullptr) {
+          edist[qi][cost_base(N) + br * S + s] = dist[s] * kScale;
+          ebits[qi][cost_base(N) + br * S + s] = bits;
+        }
       }
     }
     __syncwarp();
   }
 }
 
-template <class P, typename InT>
+// MODE 0: search every region; 1: search the listed regions; 2: evaluate the
+// given labels, one transform size EVN per launch (32 first: it initialises
+// each output with the partition's split flags; 16 and 8 then add their
+// blocks).  One size per launch keeps every warp of an SM in the same code:
+// with the three sizes mixed across warps, instruction fetch dominated.
+template <class P, typename InT, int MODE, int EVN = 0>
 __global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RdSmem& sm = *reinterpret_cast<RdSmem*>(smem_raw);
+  RdEvalSmem* ev = MODE == 2 ? reinterpret_cast<RdEvalSmem*>(smem_raw + sizeof(RdSmem)) : nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // constant tables into shared memory (per-lane indexed reads)
   {
@@ -241,25 +271,114 @@ __global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka
   int* sa = sm.a[warp];
   long long* buf = sm.buf[warp];
   u128 (*cost)[21] = sm.cost[warp];
+  u128 (*edist)[21] = MODE == 2 ? ev->dist[warp] : nullptr;
+  int (*ebits)[21] = MODE == 2 ? ev->bits[warp] : nullptr;
+  const unsigned all = (1u << ka.nq) - 1u;
+  long long count = ka.n_regions;
+  if (MODE == 1) {
+    count = *ka.subset_count;
+    count = count < ka.max_count ? count : ka.max_count;
+  }
   const long long stride = static_cast<long long>(gridDim.x) * kRdWarps;
-  for (long long reg = static_cast<long long>(blockIdx.x) * kRdWarps + warp; reg < ka.n_regions; reg += stride) {
+  for (long long k = static_cast<long long>(blockIdx.x) * kRdWarps + warp; k < count; k += stride) {
+    const long long reg = MODE == 1 ? ka.subset[k] : k;
+    if (reg < 0 || reg >= ka.n_regions) continue;
     const int img = static_cast<int>(reg / ka.tiles_per_img);
     const int t = static_cast<int>(reg - static_cast<long long>(img) * ka.tiles_per_img);
     const int ty = t / ka.tiles_x, tx = t - (t / ka.tiles_x) * ka.tiles_x;
     const int y0 = ty * 32, x0 = tx * 32;
     const int vrows = min(32, ka.height - y0), vcols = min(32, ka.width - x0);
-    // stage the region (edge replicated beyond the image), lane = column
-    const InT* src = static_cast<const InT*>(ka.in) + img * ka.bstride;
-    const int gx = x0 + min(lane, vcols - 1);
-#pragma unroll 4
-    for (int r = 0; r < 32; ++r) {
-      const int gy = y0 + min(r, vrows - 1);
-      sa[r * kPitch + lane] = static_cast<int>(src[gy * ka.pitch + gx]);
+    // sizes each step needs: all of them when searching, the labelled partition's when evaluating
+    unsigned need32 = all, need16 = all, need8 = all;
+    int lab_q = 0;
+    if (MODE == 2) {
+      need32 = need16 = need8 = 0;
+      for (int qi = 0; qi < ka.nq; ++qi) {
+        int l = ka.in_labels[static_cast<long long>(qi) * ka.n_regions + reg];
+        l = l < 17 ? l : 0;
+        if (lane == qi) lab_q = l;
+        if (l == 0) need32 |= 1u << qi;
+        else {
+          if (l - 1 != 15) need16 |= 1u << qi;
+          if (l - 1 != 0) need8 |= 1u << qi;
+        }
+      }
+      if (EVN != 32) need32 = 0;
+      if (EVN != 16) need16 = 0;
+      if (EVN != 8) need8 = 0;
+      if (EVN != 32 && (need16 | need8) == 0) continue;   // nothing of this size to add (warp-uniform)
     }
-    __syncwarp();
-    rd_size<32, P>(ka, sm, sa, buf, cost, lane, vrows, vcols);
-    rd_size<16, P>(ka, sm, sa, buf, cost, lane, vrows, vcols);
-    rd_size<8, P>(ka, sm, sa, buf, cost, lane, vrows, vcols);
+    if ((need32 | need16 | need8) != 0) {
+      // stage the region (edge replicated beyond the image), lane = column
+      const InT* src = static_cast<const InT*>(ka.in) + img * ka.bstride;
+      const int gx = x0 + min(lane, vcols - 1);
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int gy = y0 + min(r, vrows - 1);
+        sa[r * kPitch + lane] = static_cast<int>(src[gy * ka.pitch + gx]);
+      }
+      __syncwarp();
+    }
+    if ((MODE != 2 || EVN == 32) && need32)
+      rd_size<32, P>(ka, sm, sa, buf, cost, lane, vrows, vcols, need32, edist, ebits);
+    if ((MODE != 2 || EVN == 16) && need16)
+      rd_size<16, P>(ka, sm, sa, buf, cost, lane, vrows, vcols, need16, edist, ebits);
+    if ((MODE != 2 || EVN == 8) && need8)
+      rd_size<8, P>(ka, sm, sa, buf, cost, lane, vrows, vcols, need8, edist, ebits);
+    if (MODE == 2) {
+      // this size's share of the labelled partition's cost, distortion and rate, one lane per q
+      if (lane < ka.nq) {
+        const int qi = lane;
+        const u128 lam = (static_cast<u128>(ka.lam_hi[qi]) << 64) | ka.lam_lo[qi];
+        const u128* bc = cost[qi];
+        const long long o = static_cast<long long>(qi) * ka.n_regions + reg;
+        u128 j = 0, d = 0;
+        int bits = 0;
+        if (EVN == 32) {                       // split flags, and the whole region if unsplit
+          if (lab_q == 0) {
+            j = lam + bc[0];
+            d = edist[qi][0];
+            bits = 1 + ebits[qi][0];
+          } else {
+            j = lam * 5u;
+            bits = 5;
+          }
+        } else {
+          j = (static_cast<u128>(ka.ev_cost[2 * o + 1]) << 64) | ka.ev_cost[2 * o];
+          if (ka.ev_dist != nullptr) d = (static_cast<u128>(ka.ev_dist[2 * o + 1]) << 64) | ka.ev_dist[2 * o];
+          if (ka.ev_bits != nullptr) bits = ka.ev_bits[o];
+          if (lab_q != 0) {
+            const int m = lab_q - 1;
+            for (int q4 = 0; q4 < 4; ++q4) {
+              const bool split = (m >> q4) & 1;
+              if (EVN == 16 && !split) {
+                j += bc[1 + q4];
+                d += edist[qi][1 + q4];
+                bits += ebits[qi][1 + q4];
+              } else if (EVN == 8 && split) {
+                const int qy = q4 >> 1, qx = q4 & 1;
+                for (int dy = 0; dy < 2; ++dy)
+                  for (int dx = 0; dx < 2; ++dx) {
+                    const int bi = 5 + (2 * qy + dy) * 4 + 2 * qx + dx;
+                    j += bc[bi];
+                    d += edist[qi][bi];
+                    bits += ebits[qi][bi];
+                  }
+              }
+            }
+          }
+        }
+        ka.ev_cost[2 * o] = static_cast<unsigned long long>(j);
+        ka.ev_cost[2 * o + 1] = static_cast<unsigned long long>(j >> 64);
+        if (ka.ev_dist != nullptr) {
+          ka.ev_dist[2 * o] = static_cast<unsigned long long>(d);
+          ka.ev_dist[2 * o + 1] = static_cast<unsigned long long>(d >> 64);
+        }
+        if (ka.ev_bits != nullptr) ka.ev_bits[o] = bits;
+      }
+      __syncwarp();
+      continue;
+    }
     // bottom-up choice, one lane per q (ties keep the larger transform)
     if (lane < ka.nq) {
       const int qi = lane;
@@ -268,14 +387,14 @@ __global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka
       u128 j16[4], j8[4];
       int m = 0;
       u128 split = lam;
-      for (int k = 0; k < 4; ++k) {
-        const int qy = k >> 1, qx = k & 1;
-        j16[k] = lam + bc[1 + k];
-        j8[k] = lam;
+      for (int k4 = 0; k4 < 4; ++k4) {
+        const int qy = k4 >> 1, qx = k4 & 1;
+        j16[k4] = lam + bc[1 + k4];
+        j8[k4] = lam;
         for (int dy = 0; dy < 2; ++dy)
-          for (int dx = 0; dx < 2; ++dx) j8[k] += bc[5 + (2 * qy + dy) * 4 + 2 * qx + dx];
-        if (j8[k] < j16[k]) { m |= 1 << k; split += j8[k]; }
-        else split += j16[k];
+          for (int dx = 0; dx < 2; ++dx) j8[k4] += bc[5 + (2 * qy + dy) * 4 + 2 * qx + dx];
+        if (j8[k4] < j16[k4]) { m |= 1 << k4; split += j8[k4]; }
+        else split += j16[k4];
       }
       const u128 whole = lam + bc[0];
       ka.labels[static_cast<long long>(qi) * ka.n_regions + reg] =
@@ -286,7 +405,7 @@ __global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka
         pc[1] = static_cast<unsigned long long>(whole >> 64);
         for (int mm = 0; mm < 16; ++mm) {
           u128 j = lam;
-          for (int k = 0; k < 4; ++k) j += ((mm >> k) & 1) ? j8[k] : j16[k];
+          for (int k4 = 0; k4 < 4; ++k4) j += ((mm >> k4) & 1) ? j8[k4] : j16[k4];
           pc[2 + 2 * mm] = static_cast<unsigned long long>(j);
           pc[3 + 2 * mm] = static_cast<unsigned long long>(j >> 64);
         }
@@ -296,21 +415,31 @@ __global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka
   }
 }
 
-template <class P, typename InT>
+template <class P, typename InT, int MODE, int EVN = 0>
 int launch_rd_t(const RdKernelArgs& ka, int num_sms, void* stream) {
-  auto kern = rd_kernel<P, InT>;
-  const size_t smem = sizeof(RdSmem);
+  auto kern = rd_kernel<P, InT, MODE, EVN>;
+  const size_t smem = sizeof(RdSmem) + (MODE == 2 ? sizeof(RdEvalSmem) : 0);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRdThreads, smem);
   if (e != cudaSuccess) return static_cast<int>(e);
-  const long long ctas = (ka.n_regions + kRdWarps - 1) / kRdWarps;
+  const long long work = MODE == 1 ? ka.max_count : ka.n_regions;
+  const long long ctas = (work + kRdWarps - 1) / kRdWarps;
   const long long cap = static_cast<long long>(num_sms) * (occ > 0 ? occ : 1) * 8;
   const int grid = static_cast<int>(ctas < cap ? ctas : cap);
   if (grid <= 0) return 0;
   kern<<<grid, kRdThreads, smem, static_cast<cudaStream_t>(stream)>>>(ka);
   return static_cast<int>(cudaGetLastError());
+}
+
+template <int MODE, int EVN = 0>
+int launch_rd_mode(int variant, int dtype, const RdKernelArgs& ka, int num_sms, void* stream) {
+  if (variant == 1)
+    return dtype == 0 ? launch_rd_t<ParamsTilde, uint8_t, MODE, EVN>(ka, num_sms, stream)
+                      : launch_rd_t<ParamsTilde, int16_t, MODE, EVN>(ka, num_sms, stream);
+  return dtype == 0 ? launch_rd_t<ParamsHat, uint8_t, MODE, EVN>(ka, num_sms, stream)
+                    : launch_rd_t<ParamsHat, int16_t, MODE, EVN>(ka, num_sms, stream);
 }
 
 }  // namespace
@@ -361,7 +490,7 @@ void rd_tables(int variant, int* out) {
 int launch_rd(int variant, int dtype, const void* in, long long pitch, long long bstride, int width, int height,
               int batch, const int* host_tables, const int* q, int nq, const unsigned long long* lam_lo,
               const unsigned long long* lam_hi, unsigned char* labels, unsigned long long* part_cost, int num_sms,
-              void* stream) {
+              void* stream, const RdModeArgs* mode) {
   RdKernelArgs ka;
   ka.in = in;
   ka.pitch = pitch;
@@ -380,11 +509,29 @@ int launch_rd(int variant, int dtype, const void* in, long long pitch, long long
   for (int t = 0; t < rd_table_words(); ++t) ka.tables[t] = host_tables[t];
   ka.labels = labels;
   ka.part_cost = part_cost;
-  if (variant == 1)
-    return dtype == 0 ? launch_rd_t<ParamsTilde, uint8_t>(ka, num_sms, stream)
-                      : launch_rd_t<ParamsTilde, int16_t>(ka, num_sms, stream);
-  return dtype == 0 ? launch_rd_t<ParamsHat, uint8_t>(ka, num_sms, stream)
-                    : launch_rd_t<ParamsHat, int16_t>(ka, num_sms, stream);
+  ka.subset = nullptr;
+  ka.subset_count = nullptr;
+  ka.max_count = 0;
+  ka.in_labels = nullptr;
+  ka.ev_cost = nullptr;
+  ka.ev_dist = nullptr;
+  ka.ev_bits = nullptr;
+  if (mode == nullptr || mode->mode == 0) return launch_rd_mode<0>(variant, dtype, ka, num_sms, stream);
+  if (mode->mode == 1) {
+    ka.subset = mode->subset;
+    ka.subset_count = mode->subset_count;
+    ka.max_count = mode->max_count;
+    return launch_rd_mode<1>(variant, dtype, ka, num_sms, stream);
+  }
+  ka.in_labels = mode->in_labels;
+  ka.ev_cost = mode->ev_cost;
+  ka.ev_dist = mode->ev_dist;
+  ka.ev_bits = mode->ev_bits;
+  // one launch per size, in order: 32 initialises the outputs, 16 and 8 add to them
+  int rc = launch_rd_mode<2, 32>(variant, dtype, ka, num_sms, stream);
+  if (rc == 0) rc = launch_rd_mode<2, 16>(variant, dtype, ka, num_sms, stream);
+  if (rc == 0) rc = launch_rd_mode<2, 8>(variant, dtype, ka, num_sms, stream);
+  return rc;
 }
 
 }  // namespace cdct

@@ -106,3 +106,23 @@ def residual_regions_32(n_regions: int, seed: int = 4, side: int = 512):
         d = (a - b).reshape(side // 32, 32, side // 32, 32).swapaxes(1, 2).reshape(per, 32, 32)
         out[p * per:(p + 1) * per] = d
     return out[:n_regions]
+
+
+# Parameter tensors of the CNN size selector in the order of the library's
+# flat float32 vector (include/cdct.h): (name, element count, fan-in).
+CNN_LAYOUT = (("W1", 16 * 9, 9), ("b1", 16, 0), ("W2", 32 * 144, 144), ("b2", 32, 0),
+              ("W3", 32 * 288, 288), ("b3", 32, 0), ("Wf1", 64 * 512, 512), ("Wq", 64 * 4, 512),
+              ("bf1", 64, 0), ("Wf2", 17 * 64, 64), ("bf2", 17, 0))
+
+
+def cnn_init_params(seed: int = 0, bias_std: float = 0.0) -> np.ndarray:
+    """Seeded He-normal weights (std sqrt(2 / fan-in)) and N(0, bias_std) biases,
+    as the flat float32 vector of the CNN size selector."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for _, n, fan_in in CNN_LAYOUT:
+        if fan_in:
+            parts.append(rng.standard_normal(n) * math.sqrt(2.0 / fan_in))
+        else:
+            parts.append(rng.standard_normal(n) * bias_std)
+    return np.concatenate(parts).astype(np.float32)

@@ -1,0 +1,87 @@
+"""CNN selector entry points without a GPU: the flat parameter layout agrees
+between the header, the seeded initialiser and the oracle, and invalid calls
+are rejected before any launch."""
+import ctypes
+
+import numpy as np
+
+from oracle import cnn
+from paper_2207_11638_gb300 import binding as b
+from paper_2207_11638_gb300 import synth
+from tests.cnn_util import from_oracle, to_oracle
+
+
+def test_layouts_agree():
+    assert b.CNN_PARAMS == cnn.param_count() == sum(n for _, n, _ in synth.CNN_LAYOUT)
+    assert [n for _, n, _ in synth.CNN_LAYOUT] == [int(np.prod(s)) for _, s in cnn.PARAM_SHAPES]
+    flat = synth.cnn_init_params(3, bias_std=0.1)
+    assert np.array_equal(from_oracle(to_oracle(flat)), flat.astype(np.float64))
+    # He-normal spread per weight tensor
+    p = to_oracle(synth.cnn_init_params(0))
+    assert abs(np.std(p["fc1_w"]) - np.sqrt(2 / 512)) < 0.01 * np.sqrt(2 / 512) * 10
+    assert not np.any(p["conv2_b"])
+
+
+def test_packed_size_and_workspace():
+    lib = b.lib()
+    assert lib.cdct_cnn_packed_bytes() % 256 == 0 and lib.cdct_cnn_packed_bytes() >= 2 * 48241 // 2
+    n = ctypes.c_size_t()
+    assert lib.cdct_cnn_workspace_size(64, ctypes.byref(n)) == 0
+    small = n.value
+    assert lib.cdct_cnn_workspace_size(256, ctypes.byref(n)) == 0
+    assert n.value > 3 * small and n.value % 256 == 0
+    for bad in (0, 32, 100, -64):
+        assert lib.cdct_cnn_workspace_size(bad, ctypes.byref(n)) == b.CDCT_EINVAL
+
+
+def test_cnn_argument_checks_reject_before_launch():
+    lib = b.lib()
+    fake = ctypes.c_void_p(0x200000)
+    d = b.CdctImage(0x100000, 1, 64, 64, 64, 1, 0)
+    slots = (ctypes.c_int32 * 3)(0, 1, 2)
+    bad_slots = (ctypes.c_int32 * 2)(0, 4)
+    assert lib.cdct_cnn_pack(None, fake, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_pack(fake, ctypes.c_void_p(0x200004), None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_infer(fake, ctypes.byref(d), slots, 0, fake, None, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_infer(fake, ctypes.byref(d), slots, 5, fake, None, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_infer(fake, ctypes.byref(d), bad_slots, 2, fake, None, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_infer(fake, ctypes.byref(d), slots, 3, None, None, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_infer(None, ctypes.byref(d), slots, 3, fake, None, None, None) == b.CDCT_EINVAL
+    bad_img = b.CdctImage(0x100000, 7, 64, 64, 64, 1, 0)
+    assert lib.cdct_cnn_infer(fake, ctypes.byref(bad_img), slots, 3, fake, None, None, None) == b.CDCT_EINVAL
+    ws = ctypes.c_void_p(0x300000)
+    for batch in (0, 63, 100):
+        assert lib.cdct_cnn_grad(fake, fake, batch, slots, 3, fake, None, 0.0, fake, fake, ws, 1 << 30,
+                                 None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_grad(fake, fake, 64, slots, 3, fake, None, -1.0, fake, fake, ws, 1 << 30, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_grad(fake, fake, 64, slots, 3, fake, None, 0.0, fake, fake, ws, 16, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_grad(fake, fake, 64, slots, 3, fake, None, 0.0, fake, fake, ctypes.c_void_p(0x300010),
+                             1 << 30, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_grad(fake, None, 64, slots, 3, fake, None, 0.0, fake, fake, ws, 1 << 30, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_adam(fake, fake, fake, fake, 0, 1e-3, 0.9, 0.999, 1e-8, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_adam(fake, fake, fake, fake, 1, 0.0, 0.9, 0.999, 1e-8, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_adam(fake, fake, fake, fake, 1, 1e-3, 1.0, 0.999, 1e-8, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_adam(fake, None, fake, fake, 1, 1e-3, 0.9, 0.999, 1e-8, None) == b.CDCT_EINVAL
+
+
+def test_fallback_and_evaluate_argument_checks():
+    lib = b.lib()
+    fake = ctypes.c_void_p(0x200000)
+    d = b.CdctImage(0x100000, 1, 64, 64, 64, 1, 0)      # 4 regions
+    q = (ctypes.c_int32 * 3)(8, 16, 32)
+    rd = b.RdSearch("hat")
+    h = rd._h
+    assert lib.cdct_rd_search_subset(h, ctypes.byref(d), q, 3, 1, 2, None, fake, 4, fake, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_rd_search_subset(h, ctypes.byref(d), q, 3, 1, 2, fake, None, 4, fake, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_rd_search_subset(h, ctypes.byref(d), q, 3, 1, 2, fake, fake, 5, fake, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_rd_search_subset(h, ctypes.byref(d), q, 0, 1, 2, fake, fake, 4, fake, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_rd_search_subset(None, ctypes.byref(d), q, 3, 1, 2, fake, fake, 4, fake, None, None) == b.CDCT_EINVAL
+    # max_count 0: nothing to do, nothing launched
+    assert lib.cdct_rd_search_subset(h, ctypes.byref(d), q, 3, 1, 2, fake, fake, 0, fake, None, None) == b.CDCT_OK
+    assert lib.cdct_rd_evaluate(h, ctypes.byref(d), q, 3, 1, 2, fake, None, None, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_rd_evaluate(h, ctypes.byref(d), q, 3, 1, 2, None, fake, None, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_rd_evaluate(h, ctypes.byref(d), q, 3, 2000, 2, fake, fake, None, None, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_select(fake, 10, 0, 0.5, fake, fake, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_select(fake, 10, 5, 0.5, fake, fake, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_select(None, 10, 3, 0.5, fake, fake, None) == b.CDCT_EINVAL
+    assert lib.cdct_cnn_select(fake, 10, 3, float("nan"), fake, fake, None) == b.CDCT_EINVAL
