@@ -271,6 +271,69 @@ __device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up
   return acc;
 }
 
+// Coalesced output of interior blocks (N = 16, 32).  Row r of the thread's
+// block is converted as in store_row but written to the warp's staging
+// buffer `obuf` (the exchange buffer, idle by then) instead of global
+// memory; the warp then writes whole image-row segments of its adjacent
+// blocks (copy_out).  Storing a block's rows straight from the threads that
+// own them makes every 128-bit store touch one cache line per lane.
+//   N = 16: staging row pitch 128 floats (8 blocks x 16), chunk c of block b
+//           at physical chunk c ^ ((b >> 1) & 3) (conflict-free writes);
+//   N = 32: staging row pitch 68 floats (2 blocks x 32 + 4 pad).
+template <int N, typename InT>
+__device__ __forceinline__ float stage_out_row(const BlockArgs& a, const unsigned char* stage, int lb, int r,
+                                               const int (&x)[N], float* obuf, int lbw) {
+  typedef PipeGeo<N, InT> PG;
+  const f32x2 sc2 = pk2(a.scale, a.scale);
+  f32x2 rec2[N / 2];
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j)
+    rec2[j] = mul2(pk2(static_cast<float>(x[2 * j]), static_cast<float>(x[2 * j + 1])), sc2);
+  float rec[N];
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) unpk2(rec2[j], rec[2 * j], rec[2 * j + 1]);
+  float* orow = N == 16 ? obuf + r * 128 + lbw * 16 : obuf + r * 68 + lbw * 32;
+  const int swz = N == 16 ? ((lbw >> 1) & 3) : 0;
+#pragma unroll
+  for (int c = 0; c < N / 4; ++c)
+    *reinterpret_cast<float4*>(orow + 4 * (c ^ swz)) = make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2],
+                                                                   rec[4 * c + 3]);
+  if (a.partial == nullptr) return 0.f;
+  const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
+  float lo, hi;
+  unpk2(row_error<N, InT>(row, rec2, pk2(0.f, 0.f)), lo, hi);
+  return lo + hi;
+}
+
+// Write the staged rows of the warp's blocks (N rows, each one contiguous
+// segment of 8 x 16 or 2 x 32 floats starting at `base`, the first block's
+// row 0) with 128-bit streaming stores that each cover whole cache lines.
+template <int N>
+__device__ __forceinline__ void copy_out(const float* obuf, float* base, long long pitch, int lane) {
+  if constexpr (N == 16) {
+    const int b = lane >> 2, c = (lane & 3) ^ ((b >> 1) & 3);
+#pragma unroll 4
+    for (int r = 0; r < 16; ++r)
+      __stcs(reinterpret_cast<float4*>(base + r * pitch + b * 16 + c * 4),
+             *reinterpret_cast<const float4*>(obuf + r * 128 + lane * 4));
+  } else {
+    const int h = lane >> 4, ch = lane & 15;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+      const int r = 2 * k + h;
+      __stcs(reinterpret_cast<float4*>(base + r * pitch + ch * 4),
+             *reinterpret_cast<const float4*>(obuf + r * 68 + ch * 4));
+    }
+  }
+}
+
+__device__ __forceinline__ float* warp_base(float* orow0, int src_lane) {
+  const unsigned long long v = reinterpret_cast<unsigned long long>(orow0);
+  const unsigned lo = __shfl_sync(0xffffffffu, static_cast<unsigned>(v), src_lane);
+  const unsigned hi = __shfl_sync(0xffffffffu, static_cast<unsigned>(v >> 32), src_lane);
+  return reinterpret_cast<float*>((static_cast<unsigned long long>(hi) << 32) | lo);
+}
+
 __device__ __forceinline__ int32_t* kept_ptr(const BlockArgs& a, const UnitPos& up) {
   if (a.kept == nullptr || !up.active) return nullptr;
   return static_cast<int32_t*>(a.kept) +
@@ -361,7 +424,7 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
         for (int ch = 0; ch < 2; ++ch) st_v4(sb + off(0, i, ch), &v[i][4 * ch]);
     }
     __syncwarp();
-    float acc = 0.f;
+    int xr[4][16];                          // rows p, 15-p, 7-p, 8+p
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       // vertical unfold: half 0 yields rows p and 15-p, half 1 rows 7-p and 8+p:
@@ -384,12 +447,26 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
           else { hi_s[j] = t[j] + u[j]; hi_d[j] = t[j] - u[j]; }
         }
       }
-      int xs[16], xd[16];
-      madd_join<16>(lo_s, hi_s, xs);        // horizontal unfold
-      madd_join<16>(lo_d, hi_d, xd);
-      const int r0 = half == 0 ? p : 7 - p;
-      acc += store_row<16, InT>(a, up, stage, lb, r0, xs);
-      acc += store_row<16, InT>(a, up, stage, lb, 15 - r0, xd);
+      madd_join<16>(lo_s, hi_s, xr[2 * half]);        // horizontal unfold
+      madd_join<16>(lo_d, hi_d, xr[2 * half + 1]);
+    }
+    __syncwarp();                           // every unfold read of the exchange buffer is done
+    float acc = 0.f;
+    if (__all_sync(0xffffffffu, up.fast)) {
+      float* obuf = reinterpret_cast<float*>(xch);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r0 = (k >> 1) == 0 ? p : 7 - p;
+        acc += stage_out_row<16, InT>(a, stage, lb, (k & 1) ? 15 - r0 : r0, xr[k], obuf, lbw);
+      }
+      __syncwarp();
+      copy_out<16>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r0 = (k >> 1) == 0 ? p : 7 - p;
+        acc += store_row<16, InT>(a, up, stage, lb, (k & 1) ? 15 - r0 : r0, xr[k]);
+      }
     }
     __syncwarp();
     return acc;
@@ -498,8 +575,10 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
         }
       }
     }
-    __syncwarp();
+    __syncwarp();                                  // every unfold read of the exchange buffer is done
     float acc = 0.f;
+    const bool co = __all_sync(0xffffffffu, up.fast);
+    float* obuf = reinterpret_cast<float*>(xch);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       int cc[4][8];
@@ -511,8 +590,14 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
       madd_join<16>(cc[0], cc[1], lo);             // horizontal unfold, second level
       madd_join<16>(cc[2], cc[3], hi);
       madd_join<32>(lo, hi, x);                    // first level
-      acc += store_row<32, InT>(a, up, stage, lb, t == 0 ? p : 31 - p, x);
+      if (co) acc += stage_out_row<32, InT>(a, stage, lb, t == 0 ? p : 31 - p, x, obuf, lbw);
+      else acc += store_row<32, InT>(a, up, stage, lb, t == 0 ? p : 31 - p, x);
     }
+    if (co) {
+      __syncwarp();
+      copy_out<32>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane);
+    }
+    __syncwarp();
     return acc;
   }
 };
