@@ -132,6 +132,20 @@ cdct_status cdct_psnr(const cdct_image* ref, const float* recon, int64_t recon_p
                       int64_t recon_batch_stride, double* psnr_db, void* workspace,
                       size_t workspace_bytes, void* stream);
 
+/* SSIM (Sec. 5.1 reports it beside PSNR; the paper cites the index of Wang
+ * et al. without restating it): ssim[b] = mean over every 11 x 11 window
+ * inside image b of
+ *   (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_xx + s_yy + C2)),
+ * the statistics weighted by a unit-sum circular Gaussian window (sigma 1.5),
+ * C1 = (0.01 * 255)^2, C2 = (0.03 * 255)^2, x the reference, y the
+ * reconstruction.  Images must be at least 11 x 11.  ssim is a device array
+ * of `ref->batch` doubles; the workspace needs cdct_ssim_workspace_size()
+ * bytes (8-byte aligned).  Computed in float64 with a fixed reduction
+ * order: reproducible bit for bit. */
+cdct_status cdct_ssim_workspace_size(const cdct_image* ref, size_t* bytes);
+cdct_status cdct_ssim(const cdct_image* ref, const float* recon, int64_t recon_pitch, int64_t recon_batch_stride,
+                      double* ssim, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Fused forward -> zonal(r) -> inverse -> PSNR in one pass over the pixels.
  * recon as for cdct_inverse; kept (NULL to skip) as for cdct_zonal; psnr_db
  * (NULL to skip) as for cdct_psnr, which then needs the workspace. */

@@ -29,6 +29,7 @@ EXPORTS = (
     "cdct_rd_create", "cdct_rd_destroy", "cdct_rd_tables", "cdct_rd_region_count", "cdct_rd_search",
     "cdct_cnn_packed_bytes", "cdct_cnn_pack", "cdct_cnn_infer", "cdct_cnn_workspace_size", "cdct_cnn_grad",
     "cdct_cnn_adam", "cdct_rd_search_subset", "cdct_rd_evaluate", "cdct_cnn_select",
+    "cdct_ssim_workspace_size", "cdct_ssim",
 )
 CNN_PARAMS, CNN_LABELS, CNN_SLOTS = 48241, 17, 4
 
@@ -99,6 +100,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                                  vp, vp]),
         "cdct_rd_evaluate": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i32), i32, i32, i32, vp, vp, vp, vp, vp]),
         "cdct_cnn_select": (ctypes.c_int, [vp, i64, i32, ctypes.c_float, vp, vp, vp]),
+        "cdct_ssim_workspace_size": (ctypes.c_int, [img_p, ctypes.POINTER(sz)]),
+        "cdct_ssim": (ctypes.c_int, [img_p, vp, i64, i64, vp, vp, sz, vp]),
         "cdct_cnn_packed_bytes": (sz, []),
         "cdct_cnn_pack": (ctypes.c_int, [vp, vp, vp]),
         "cdct_cnn_infer": (ctypes.c_int, [vp, img_p, ctypes.POINTER(i32), i32, vp, vp, vp, vp]),
@@ -483,6 +486,26 @@ class RdSearch:
                                      labels.contiguous().data_ptr(), cost.data_ptr(), dist.data_ptr(),
                                      bits.data_ptr(), stream_handle(stream)))
         return cost, dist, bits
+
+
+def ssim(ref, recon, out=None, workspace=None, stream=None):
+    """Mean SSIM per image of recon (float32 [B, H, W] or [H, W]) against ref (uint8 / int16),
+    as a device float64 tensor [B]."""
+    torch = _torch()
+    d = image_desc(ref)
+    r3 = recon if recon.dim() == 3 else recon.unsqueeze(0)
+    if r3.dtype != torch.float32 or r3.stride(2) != 1:
+        raise ValueError("recon must be float32 with contiguous rows")
+    n = ctypes.c_size_t()
+    check(lib().cdct_ssim_workspace_size(ctypes.byref(d), ctypes.byref(n)))
+    if workspace is None:
+        workspace = torch.empty(max(n.value // 8, 1), dtype=torch.float64, device=ref.device)
+    if out is None:
+        out = torch.empty(d.batch, dtype=torch.float64, device=ref.device)
+    check(lib().cdct_ssim(ctypes.byref(d), r3.data_ptr(), r3.stride(1),
+                          r3.stride(0) if d.batch > 1 else d.height * r3.stride(1), out.data_ptr(),
+                          workspace.data_ptr(), workspace.numel() * workspace.element_size(), stream_handle(stream)))
+    return out
 
 
 def cnn_select(margin, threshold: float, stream=None):

@@ -357,6 +357,31 @@ cdct_status cdct_psnr(const cdct_image* ref, const float* recon, int64_t recon_p
   return rc ? cuda_fail(rc, "psnr finalize launch") : CDCT_OK;
 }
 
+cdct_status cdct_ssim_workspace_size(const cdct_image* ref, size_t* bytes) {
+  cdct_status st = check_image(ref, "ssim");
+  if (st != CDCT_OK) return st;
+  if (bytes == nullptr) return fail(CDCT_EINVAL, "null bytes pointer");
+  if (ref->width < 11 || ref->height < 11) return fail(CDCT_EINVAL, "ssim: images must be at least 11 x 11");
+  *bytes = static_cast<size_t>(ssim_tiles(ref->width, ref->height)) * ref->batch * sizeof(double);
+  return CDCT_OK;
+}
+
+cdct_status cdct_ssim(const cdct_image* ref, const float* recon, int64_t recon_pitch, int64_t recon_batch_stride,
+                      double* ssim, void* workspace, size_t workspace_bytes, void* stream) {
+  size_t need = 0;
+  cdct_status st = cdct_ssim_workspace_size(ref, &need);
+  if (st != CDCT_OK) return st;
+  st = check_recon(recon, recon_pitch, recon_batch_stride, ref->width, ref->height, ref->batch);
+  if (st != CDCT_OK) return st;
+  if (ssim == nullptr) return fail(CDCT_EINVAL, "null ssim output");
+  if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 7u))
+    return fail(CDCT_EINVAL, "workspace missing, misaligned or smaller than cdct_ssim_workspace_size()");
+  const int rc = ssim_launch(ref->data, ref->dtype, ref->pitch, ref->batch > 1 ? ref->batch_stride : 0, recon,
+                             recon_pitch, ref->batch > 1 ? recon_batch_stride : 0, ref->width, ref->height,
+                             ref->batch, static_cast<double*>(workspace), ssim, stream);
+  return rc ? cuda_fail(rc, "ssim launch") : CDCT_OK;
+}
+
 cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, float* recon, int64_t recon_pitch,
                                int64_t recon_batch_stride, void* kept, double* psnr_db, void* workspace,
                                size_t workspace_bytes, void* stream) {

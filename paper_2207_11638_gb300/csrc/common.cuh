@@ -133,6 +133,11 @@ int launch_psnr_partials(const void* ref, int dtype, long long ref_pitch, long l
                          int width, int height, int batch, double* partial, int parts_per_img,
                          void* stream);
 int psnr_parts_per_img(int height);
+// mean SSIM per image (ssim.cu): window-position tiles per image, and the launch
+long long ssim_tiles(int width, int height);
+int ssim_launch(const void* ref, int dtype, long long ref_pitch, long long ref_bstride, const float* rec,
+                long long rec_pitch, long long rec_bstride, int width, int height, int batch, double* partial,
+                double* ssim, void* stream);
 
 // Zig-zag position of (i, j) in an n x n block (anti-diagonals in order;
 // row index falling on even diagonals, rising on odd ones).

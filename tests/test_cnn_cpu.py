@@ -85,3 +85,18 @@ def test_fallback_and_evaluate_argument_checks():
     assert lib.cdct_cnn_select(fake, 10, 5, 0.5, fake, fake, None) == b.CDCT_EINVAL
     assert lib.cdct_cnn_select(None, 10, 3, 0.5, fake, fake, None) == b.CDCT_EINVAL
     assert lib.cdct_cnn_select(fake, 10, 3, float("nan"), fake, fake, None) == b.CDCT_EINVAL
+
+
+def test_ssim_argument_checks():
+    lib = b.lib()
+    fake = ctypes.c_void_p(0x200000)
+    n = ctypes.c_size_t()
+    d = b.CdctImage(0x100000, 0, 64, 48, 64, 2, 64 * 48)
+    assert lib.cdct_ssim_workspace_size(ctypes.byref(d), ctypes.byref(n)) == b.CDCT_OK
+    assert n.value == 2 * 2 * 2 * 8          # 2 images x (54/32 -> 2) x (38/32 -> 2) tiles x 8 bytes
+    small = b.CdctImage(0x100000, 0, 10, 48, 64, 1, 0)
+    assert lib.cdct_ssim_workspace_size(ctypes.byref(small), ctypes.byref(n)) == b.CDCT_EINVAL
+    assert lib.cdct_ssim(ctypes.byref(d), fake, 64, 64 * 48, None, fake, 1 << 20, None) == b.CDCT_EINVAL
+    assert lib.cdct_ssim(ctypes.byref(d), fake, 64, 64 * 48, fake, fake, 8, None) == b.CDCT_EINVAL
+    assert lib.cdct_ssim(ctypes.byref(d), fake, 10, 64 * 48, fake, fake, 1 << 20, None) == b.CDCT_EINVAL
+    assert lib.cdct_ssim(ctypes.byref(d), None, 64, 64 * 48, fake, fake, 1 << 20, None) == b.CDCT_EINVAL
