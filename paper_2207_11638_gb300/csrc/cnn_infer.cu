@@ -42,8 +42,9 @@ constexpr int kFeatPitch = 520;                 // bf16 per feature row (512 + 8
 constexpr int kAct1Bytes = 2 * 18 * 18 * 16;    // [2 planes][18][18][8 ch] bf16
 constexpr int kBuf2Bytes = 4 * 10 * 10 * 16;    // act2 [4 planes][10][10][8 ch] bf16, or the staged region
 constexpr int kWarpBytes = kAct1Bytes + kBuf2Bytes;
+constexpr int kF2Pitch = kHidden + 1;            // Wf2 row pitch in shared memory (floats)
 constexpr int kHeadOff = static_cast<int>(kPkConvEnd);
-constexpr int kHeadBytes = static_cast<int>(kPkHeadEnd - kPkHead);
+constexpr int kHeadBytes = ((kHidden + kHidden * kSlots + kLabels * kF2Pitch + kLabels) * 4 + 15) / 16 * 16;
 constexpr int kWarpOff = kHeadOff + kHeadBytes;
 constexpr int kFeatOff = kWarpOff + kWarpsI * kWarpBytes;
 constexpr int kUOff = kFeatOff + kGroup * kFeatPitch * 2;
@@ -264,9 +265,14 @@ __global__ void __launch_bounds__(kThreadsI, 1) cnn_infer_kernel(const InferArgs
     const uint4* src = reinterpret_cast<const uint4*>(a.packed);
     uint4* dst = reinterpret_cast<uint4*>(sm);
     for (int i = tid; i < static_cast<int>(kPkConvEnd / 16); i += kThreadsI) dst[i] = src[i];
-    const uint4* hs = reinterpret_cast<const uint4*>(a.packed + kPkHead);
-    uint4* hd = reinterpret_cast<uint4*>(sm + kHeadOff);
-    for (int i = tid; i < kHeadBytes / 16; i += kThreadsI) hd[i] = hs[i];
+    // head: fb1, Wq as packed; Wf2 rows padded to 65 floats (the logit loop reads
+    // one row per label across the lanes); fb2
+    const float* hs = reinterpret_cast<const float*>(a.packed + kPkHead);
+    float* hd = reinterpret_cast<float*>(sm + kHeadOff);
+    constexpr int nq = kHidden + kHidden * kSlots;
+    for (int i = tid; i < nq; i += kThreadsI) hd[i] = hs[i];
+    for (int i = tid; i < kLabels * kHidden; i += kThreadsI) hd[nq + (i / kHidden) * kF2Pitch + i % kHidden] = hs[nq + i];
+    for (int i = tid; i < kLabels; i += kThreadsI) hd[nq + kLabels * kF2Pitch + i] = hs[nq + kLabels * kHidden + i];
   }
   unsigned char* act1 = sm + kWarpOff + warp * kWarpBytes;
   unsigned char* buf2 = act1 + kAct1Bytes;
@@ -291,8 +297,8 @@ __global__ void __launch_bounds__(kThreadsI, 1) cnn_infer_kernel(const InferArgs
   float* logit_s = reinterpret_cast<float*>(sm + kLogitOff);
   const float* fb1 = reinterpret_cast<const float*>(sm + kHeadOff);
   const float* wq = fb1 + kHidden;               // [64][4]
-  const float* wf2 = wq + kHidden * kSlots;      // [17][64]
-  const float* fb2 = wf2 + kLabels * kHidden;    // [17]
+  const float* wf2 = wq + kHidden * kSlots;      // [17][65]
+  const float* fb2 = wf2 + kLabels * kF2Pitch;   // [17]
   const int ns = a.n_slots;
 
   for (long long base = static_cast<long long>(blockIdx.x) * kGroup; base < a.n_regions;
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(kThreadsI, 1) cnn_infer_kernel(const InferArgs
         const int si = rem / kLabels, j = rem - si * kLabels;
         const int slot = a.slots[si];
         const float* ur = u_s + region * kHidden;
-        const float* w = wf2 + j * kHidden;
+        const float* w = wf2 + j * kF2Pitch;
         float acc = fb2[j];
 #pragma unroll 8
         for (int h = 0; h < kHidden; ++h) {

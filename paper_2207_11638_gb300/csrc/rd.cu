@@ -40,7 +40,9 @@ constexpr int kPitch = 33;                   // padded row pitch (words)
 
 struct RdSmem {
   int d[3][32];                              // d_i for N = 32, 16, 8
-  int c32[32 * 32], c16[16 * 16], c8[8 * 8]; // dequantisation scales
+  // dequantisation scales c_ij, rows padded to N + 1 words: lane i reads row i, so an
+  // unpadded row pitch of N would put all lanes of a read in one bank
+  int c32[32 * 33], c16[16 * 17], c8[8 * 9];
   float sd[3][32];                           // sqrt(d_j) (first guesses of the quantiser only)
   int a[kRdWarps][32 * kPitch];              // regions
   long long buf[kRdWarps][32 * kPitch];      // transposes
@@ -170,7 +172,7 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
         last[c / N] = max(last[c / N], zigzag_pos(N, i, j));
       }
       // |N q L| < 2^23 and c < 2^16: one 32 x 32 -> 64-bit product
-      buf[lane * kPitch + c] = static_cast<long long>(N * q * l) * cc[i * N + j];
+      buf[lane * kPitch + c] = static_cast<long long>(N * q * l) * cc[i * (N + 1) + j];
     }
     __syncwarp();
     // inverse, columns: (2U) Y'
@@ -261,11 +263,14 @@ __global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // constant tables into shared memory (per-lane indexed reads)
   {
-    const int total = 3 * 32 + 32 * 32 + 16 * 16 + 8 * 8;
-    int* dst = &sm.d[0][0];
-    for (int t = threadIdx.x; t < total; t += kRdThreads) dst[t] = ka.tables[t];
-    for (int t = threadIdx.x; t < 3 * 32; t += kRdThreads)
+    for (int t = threadIdx.x; t < 3 * 32; t += kRdThreads) {
+      sm.d[t / 32][t % 32] = ka.tables[t];
       sm.sd[t / 32][t % 32] = sqrtf(static_cast<float>(ka.tables[t]));
+    }
+    const int* c = ka.tables + 3 * 32;
+    for (int t = threadIdx.x; t < 32 * 32; t += kRdThreads) sm.c32[(t >> 5) * 33 + (t & 31)] = c[t];
+    for (int t = threadIdx.x; t < 16 * 16; t += kRdThreads) sm.c16[(t >> 4) * 17 + (t & 15)] = c[1024 + t];
+    for (int t = threadIdx.x; t < 8 * 8; t += kRdThreads) sm.c8[(t >> 3) * 9 + (t & 7)] = c[1024 + 256 + t];
   }
   __syncthreads();
   int* sa = sm.a[warp];
