@@ -394,7 +394,8 @@ cdct_status cdct_cnn_adam(float* params, const float* grad, float* m, float* v, 
 /* Synchronise `stream` and report whether a kernel of this library gave up
  * a bounded wait on the current device since the last check (the fused
  * kernel waits, with a time limit of about one second, for the bulk copies
- * that stage its input).  Returns CDCT_ETIMEOUT and clears the record if so,
+ * that stage its input; the training GEMMs wait as long for their tensor-core
+ * products).  Returns CDCT_ETIMEOUT and clears the record if so,
  * CDCT_OK otherwise.  Outputs of a call that timed out are incomplete. */
 cdct_status cdct_check_device(void* stream);
 

@@ -626,7 +626,8 @@ cdct_status cdct_check_device(void* stream) {
   const int zero = 0;
   rc = static_cast<int>(cudaMemcpy(di->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
   if (rc) return cuda_fail(rc, "error word reset");
-  return fail(CDCT_ETIMEOUT, "a kernel gave up waiting for its staged input (bounded wait expired)");
+  return fail(CDCT_ETIMEOUT, (word & 1) ? "a kernel gave up waiting for its staged input (bounded wait expired)"
+                                        : "a kernel gave up waiting for its tensor-core products (bounded wait expired)");
 }
 
 cdct_status cdct_rd_create(int variant, cdct_rd* out) {
@@ -845,9 +846,12 @@ cdct_status cdct_cnn_grad(const float* params, const int16_t* regions, int32_t b
   if (workspace_bytes < cnn_train_workspace(batch)) return fail(CDCT_EINVAL, "workspace too small");
   int sl[CDCT_CNN_SLOTS];
   for (int k = 0; k < n_slots; ++k) sl[k] = slots[k];
-  const int rc = cnn_grad_launch(params, regions, batch, sl, n_slots, labels,
-                                 reinterpret_cast<const unsigned long long*>(partition_cost), mu, grad, loss, workspace,
-                                 stream);
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  rc = cnn_grad_launch(params, regions, batch, sl, n_slots, labels,
+                       reinterpret_cast<const unsigned long long*>(partition_cost), mu, grad, loss, workspace, di->err,
+                       stream);
   return rc ? cuda_fail(rc, "cnn gradient launch") : CDCT_OK;
 }
 

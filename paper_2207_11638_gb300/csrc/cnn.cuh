@@ -66,7 +66,7 @@ int cnn_select_launch(const float* margin, long long n, int ns, float threshold,
 size_t cnn_train_workspace(long long batch);
 int cnn_grad_launch(const float* params, const int16_t* regions, int B, const int* slots, int ns,
                     const unsigned char* labels, const unsigned long long* pcost, float mu, float* grad,
-                    float* loss, void* workspace, void* stream);
+                    float* loss, void* workspace, int* err, void* stream);
 int cnn_adam_launch(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
                     float beta2, float eps, void* stream);
 

@@ -23,6 +23,7 @@
 #include "mma.cuh"
 #include "common.cuh"
 #include "ptx.cuh"
+#include "tcgen05.cuh"
 
 namespace cdct {
 namespace {
@@ -30,96 +31,125 @@ namespace {
 using namespace cnn;
 
 // ---------------------------------------------------------------------------
-// GEMM  C[M][N] = A[M][K] B[N][K]^T  (bf16 in, float32 accumulate), M % 64 == 0,
-// K % 16 == 0, N % 16 == 0.  A CTA of 4 warps owns 64 rows and up to 64
-// columns, with both tiles whole in shared memory (row pitch K + 8, so the
-// ldmatrix rows fall in distinct banks); warp w computes rows 16w .. 16w + 15.
-// Epilogue: float32 out, or bias + ReLU -> bf16 out.
+// GEMM  C[M][N] = A[M][K] B[N][K]^T on the tcgen05 tensor cores (bf16 in,
+// float32 accumulate in tensor memory).  K % 16 == 0, N a multiple of BN
+// (16, 32 or 64); rows of A beyond M read as zero.  A CTA of 4 warps owns a
+// 128 x BN tile:
+//   1. all threads copy the A tile (128 x K) and the B tile (BN x K) into
+//      shared memory in the no-swizzle K-major core-matrix layout, one slab
+//      per MMA (K = 16): element (r, k) of slab s = k / 16 sits at
+//      s * rows * 32 + (r / 8) * 256 + ((k / 8) % 2) * 128 + (r % 8) * 16 + (k % 8) * 2
+//      bytes, i.e. core matrices 128 B apart along K and 256 B apart along
+//      M / N; then they are fenced for the async proxy;
+//   2. one thread issues the K/16 MMAs into a 128 x BN float32 accumulator in
+//      tensor memory and commits them to an mbarrier;
+//   3. after a bounded wait, warp w loads accumulator lanes 32w .. 32w + 31
+//      (rows of the tile) and applies the epilogue: float32 out, or
+//      bias + ReLU -> bf16.
 // ---------------------------------------------------------------------------
 constexpr int kGemmThreads = 128;
+constexpr long long kTcWaitLimit = 1ll << 31;   // SM cycles (~1 s) before a wait gives up
 
 template <int BN, bool RELU_BF16>
-__global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const uint16_t* __restrict__ A,
-                                                               const uint16_t* __restrict__ B, int N, int K,
-                                                               const float* __restrict__ bias, void* __restrict__ C) {
-  extern __shared__ __align__(16) unsigned char smg[];
-  const int pitch = K + 8;
-  uint16_t* sa = reinterpret_cast<uint16_t*>(smg);
-  uint16_t* sb = sa + 64 * pitch;
+__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const uint16_t* __restrict__ A,
+                                                               const uint16_t* __restrict__ B, long long M, int N,
+                                                               int K, const float* __restrict__ bias,
+                                                               void* __restrict__ C, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smg[];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_base;
+  constexpr uint32_t kCols = BN < 32 ? 32 : BN;
+  constexpr uint32_t kSlabA = 128 * 32, kSlabB = BN * 32;   // bytes per K = 16 slab
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long m0 = static_cast<long long>(blockIdx.x) * 64;
+  const long long m0 = static_cast<long long>(blockIdx.x) * 128;
   const int n0 = blockIdx.y * BN;
-  const int kv = K / 8;   // uint4 per row
-  for (int i = tid; i < 64 * kv; i += kGemmThreads) {
-    const int r = i / kv, c = i - r * kv;
-    *reinterpret_cast<uint4*>(sa + r * pitch + c * 8) =
-        *reinterpret_cast<const uint4*>(A + (m0 + r) * K + c * 8);
+  unsigned char* sa = smg;
+  unsigned char* sb = smg + static_cast<size_t>(K) * 128 * 2;
+  const int kc_n = K / 8;
+  for (int i = tid; i < kc_n * 128; i += kGemmThreads) {
+    const int kc = i >> 7, r = i & 127;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (m0 + r < M) v = *reinterpret_cast<const uint4*>(A + (m0 + r) * K + kc * 8);
+    *reinterpret_cast<uint4*>(sa + (kc >> 1) * kSlabA + (r >> 3) * 256 + (kc & 1) * 128 + (r & 7) * 16) = v;
   }
-  for (int i = tid; i < BN * kv; i += kGemmThreads) {
-    const int r = i / kv, c = i - r * kv;
-    *reinterpret_cast<uint4*>(sb + r * pitch + c * 8) =
-        *reinterpret_cast<const uint4*>(B + static_cast<long long>(n0 + r) * K + c * 8);
+  for (int i = tid; i < kc_n * BN; i += kGemmThreads) {
+    const int kc = i / BN, r = i - kc * BN;
+    *reinterpret_cast<uint4*>(sb + (kc >> 1) * kSlabB + (r >> 3) * 256 + (kc & 1) * 128 + (r & 7) * 16) =
+        *reinterpret_cast<const uint4*>(B + static_cast<long long>(n0 + r) * K + kc * 8);
   }
+  fence_proxy_async_smem();                // the copies above are read by the tensor cores
+  if (warp == 0) tmem_alloc(&tmem_base, kCols);
+  if (tid == 0) {
+    mbar_init(&done, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
   __syncthreads();
-  float acc[BN / 8][4];
-#pragma unroll
-  for (int j = 0; j < BN / 8; ++j)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
-  const uint32_t a_lane =
-      smem_u32(sa) + ((warp * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * pitch + (lane >> 4) * 8) * 2;
-  const uint32_t b_lane = smem_u32(sb) + (((lane & 7) + (lane >> 4) * 8) * pitch + ((lane >> 3) & 1) * 8) * 2;
-  for (int k = 0; k < K; k += 16) {
-    uint32_t af[4];
-    ldsm_x4(af, a_lane + k * 2);
-#pragma unroll
-    for (int p = 0; p < BN / 16; ++p) {
-      uint32_t bf[4];
-      ldsm_x4(bf, b_lane + (p * 16 * pitch + k) * 2);
-      const uint32_t b0[2] = {bf[0], bf[1]}, b1[2] = {bf[2], bf[3]};
-      mma_bf16(acc[2 * p], af, b0);
-      mma_bf16(acc[2 * p + 1], af, b1);
-    }
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
+    const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+    for (int kk = 0; kk < K / 16; ++kk)
+      umma_bf16(tmem, umma_desc(a0 + kk * kSlabA, 128, 256), umma_desc(b0 + kk * kSlabB, 128, 256), idesc,
+                kk > 0 ? 1u : 0u);
+    umma_commit(&done);
   }
-  const int g = lane >> 2, t = lane & 3;
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&done, 0, kTcWaitLimit));
+  tc_fence_after();
+  if (ok) {
+    const long long row = m0 + warp * 32 + lane;
 #pragma unroll
-  for (int j = 0; j < BN / 8; ++j) {
-    const int col = n0 + j * 8 + 2 * t;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+      if (row < M) {
+        const int col = n0 + c0;
+        if (RELU_BF16) {
+          uint32_t w[8];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const long long row = m0 + warp * 16 + g + 8 * h;
-      float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
-      if (RELU_BF16) {
-        v0 = fmaxf(v0 + bias[col], 0.f);
-        v1 = fmaxf(v1 + bias[col + 1], 0.f);
-        *reinterpret_cast<uint32_t*>(static_cast<uint16_t*>(C) + row * N + col) = pack_bf16(v0, v1);
-      } else {
-        *reinterpret_cast<float2*>(static_cast<float*>(C) + row * N + col) = make_float2(v0, v1);
+          for (int j = 0; j < 8; ++j)
+            w[j] = pack_bf16(fmaxf(v[2 * j] + bias[col + 2 * j], 0.f), fmaxf(v[2 * j + 1] + bias[col + 2 * j + 1], 0.f));
+          uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(C) + row * N + col);
+          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(C) + row * N + col);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
       }
     }
+  } else if (tid == 0) {
+    atomicOr(err, 2);
+    // the MMAs may still be running: wait for them (bounded) before freeing their memory
+    (void)mbar_wait_bounded(&done, 0, kTcWaitLimit);
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
 template <int BN, bool RELU_BF16>
 int gemm_launch_t(const uint16_t* A, const uint16_t* B, long long M, int N, int K, const float* bias, void* C,
-                  cudaStream_t s) {
-  const int smem = (64 + BN) * (K + 8) * 2;
-  auto kern = gemm_nt_kernel<BN, RELU_BF16>;
+                  int* err, cudaStream_t s) {
+  const int smem = (128 + BN) * K * 2;
+  auto kern = gemm_tc_kernel<BN, RELU_BF16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return static_cast<int>(e);
-  dim3 grid(static_cast<unsigned>(M / 64), static_cast<unsigned>(N / BN));
-  kern<<<grid, kGemmThreads, smem, s>>>(A, B, N, K, bias, C);
+  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>(N / BN));
+  kern<<<grid, kGemmThreads, smem, s>>>(A, B, M, N, K, bias, C, err);
   return static_cast<int>(cudaGetLastError());
 }
 
 int gemm(const uint16_t* A, const uint16_t* B, long long M, int N, int K, const float* bias, void* C, bool relu_bf16,
-         cudaStream_t s) {
-  if (N == 16) return relu_bf16 ? gemm_launch_t<16, true>(A, B, M, N, K, bias, C, s)
-                                : gemm_launch_t<16, false>(A, B, M, N, K, bias, C, s);
-  if (N == 32) return relu_bf16 ? gemm_launch_t<32, true>(A, B, M, N, K, bias, C, s)
-                                : gemm_launch_t<32, false>(A, B, M, N, K, bias, C, s);
-  return relu_bf16 ? gemm_launch_t<64, true>(A, B, M, N, K, bias, C, s)
-                   : gemm_launch_t<64, false>(A, B, M, N, K, bias, C, s);
+         int* err, cudaStream_t s) {
+  if (N == 16) return relu_bf16 ? gemm_launch_t<16, true>(A, B, M, N, K, bias, C, err, s)
+                                : gemm_launch_t<16, false>(A, B, M, N, K, bias, C, err, s);
+  if (N == 32) return relu_bf16 ? gemm_launch_t<32, true>(A, B, M, N, K, bias, C, err, s)
+                                : gemm_launch_t<32, false>(A, B, M, N, K, bias, C, err, s);
+  return relu_bf16 ? gemm_launch_t<64, true>(A, B, M, N, K, bias, C, err, s)
+                   : gemm_launch_t<64, false>(A, B, M, N, K, bias, C, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,7 +635,7 @@ size_t cnn_train_workspace(long long batch) { return carve(nullptr, batch).bytes
 // Loss and gradient of one batch (see the file comment).  Returns a cudaError_t code.
 int cnn_grad_launch(const float* params, const int16_t* regions, int B, const int* slots, int ns,
                     const unsigned char* labels, const unsigned long long* pcost, float mu, float* grad,
-                    float* loss, void* workspace, void* stream) {
+                    float* loss, void* workspace, int* err, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TrainWs w = carve(workspace, B);
   const long long b = B;
@@ -617,20 +647,20 @@ int cnn_grad_launch(const float* params, const int16_t* regions, int B, const in
   // forward
   im2col_input_kernel<<<grid_for(b * 1024), 256, 0, s>>>(regions, b * 1024, w.A1);
   CNN_LAUNCHED();
-  CNN_CHECK(gemm(w.A1, w.w1, b * 1024, 16, 16, params + kOffB1, w.R1, true, s));
+  CNN_CHECK(gemm(w.A1, w.w1, b * 1024, 16, 16, params + kOffB1, w.R1, true, err, s));
   pool_kernel<<<grid_for(b * 256 * 16), 256, 0, s>>>(w.R1, 32, 16, b * 256 * 16, w.P1, w.arg1);
   CNN_LAUNCHED();
   im2col_kernel<16><<<grid_for(b * 256 * 9 * 2), 256, 0, s>>>(w.P1, 16, b * 256 * 9 * 2, w.A2);
   CNN_LAUNCHED();
-  CNN_CHECK(gemm(w.A2, w.w2, b * 256, 32, 144, params + kOffB2, w.R2, true, s));
+  CNN_CHECK(gemm(w.A2, w.w2, b * 256, 32, 144, params + kOffB2, w.R2, true, err, s));
   pool_kernel<<<grid_for(b * 64 * 32), 256, 0, s>>>(w.R2, 16, 32, b * 64 * 32, w.P2, w.arg2);
   CNN_LAUNCHED();
   im2col_kernel<32><<<grid_for(b * 64 * 9 * 4), 256, 0, s>>>(w.P2, 8, b * 64 * 9 * 4, w.A3);
   CNN_LAUNCHED();
-  CNN_CHECK(gemm(w.A3, w.w3, b * 64, 32, 288, params + kOffB3, w.R3, true, s));
+  CNN_CHECK(gemm(w.A3, w.w3, b * 64, 32, 288, params + kOffB3, w.R3, true, err, s));
   pool_kernel<<<grid_for(b * 512), 256, 0, s>>>(w.R3, 8, 32, b * 512, w.H, w.arg3);
   CNN_LAUNCHED();
-  CNN_CHECK(gemm(w.H, w.f1, b, 64, 512, nullptr, w.U, false, s));
+  CNN_CHECK(gemm(w.H, w.f1, b, 64, 512, nullptr, w.U, false, err, s));
   // head
   HeadArgs ha;
   ha.p = params;
@@ -650,7 +680,7 @@ int cnn_grad_launch(const float* params, const int16_t* regions, int B, const in
                                                               ha.inv_count);
   CNN_LAUNCHED();
   // fc1 backward
-  CNN_CHECK(gemm(w.DU, w.f1t, b, 512, 64, nullptr, w.DH, false, s));
+  CNN_CHECK(gemm(w.DU, w.f1t, b, 512, 64, nullptr, w.DH, false, err, s));
   CNN_CHECK(wgrad(64, w.DU, w.H, b, 512, 512, w.wpart, w.bpart, grad + kOffF1, nullptr, s));
   // conv3
   pool_backward_kernel<<<grid_for(b * 64 * 32), 256, 0, s>>>(w.DH, w.arg3, w.R3, 8, 32, b * 64 * 32, w.DZ3);
@@ -658,14 +688,14 @@ int cnn_grad_launch(const float* params, const int16_t* regions, int B, const in
   CNN_CHECK(wgrad(32, w.DZ3, w.A3, b * 64, 288, 288, w.wpart, w.bpart, grad + kOffW3, grad + kOffB3, s));
   im2col_kernel<32><<<grid_for(b * 64 * 9 * 4), 256, 0, s>>>(w.DZ3, 8, b * 64 * 9 * 4, w.IMD);
   CNN_LAUNCHED();
-  CNN_CHECK(gemm(w.IMD, w.w3f, b * 64, 32, 288, nullptr, w.DA2, false, s));
+  CNN_CHECK(gemm(w.IMD, w.w3f, b * 64, 32, 288, nullptr, w.DA2, false, err, s));
   // conv2
   pool_backward_kernel<<<grid_for(b * 256 * 32), 256, 0, s>>>(w.DA2, w.arg2, w.R2, 16, 32, b * 256 * 32, w.DZ2);
   CNN_LAUNCHED();
   CNN_CHECK(wgrad(32, w.DZ2, w.A2, b * 256, 144, 144, w.wpart, w.bpart, grad + kOffW2, grad + kOffB2, s));
   im2col_kernel<32><<<grid_for(b * 256 * 9 * 4), 256, 0, s>>>(w.DZ2, 16, b * 256 * 9 * 4, w.IMD);
   CNN_LAUNCHED();
-  CNN_CHECK(gemm(w.IMD, w.w2f, b * 256, 16, 288, nullptr, w.DA1, false, s));
+  CNN_CHECK(gemm(w.IMD, w.w2f, b * 256, 16, 288, nullptr, w.DA1, false, err, s));
   // conv1
   pool_backward_kernel<<<grid_for(b * 1024 * 16), 256, 0, s>>>(w.DA1, w.arg1, w.R1, 32, 16, b * 1024 * 16, w.DZ1);
   CNN_LAUNCHED();
