@@ -689,9 +689,25 @@ def run_learned(args):
     # the headline: the learned decision at the smallest fallback share that keeps the held-out
     # RD-cost increase within 1 % (the network alone if none does)
     if chosen is None:
-        head_name, head_ms, head_inc = "cnn_only", ms_cnn, 100 * dj(j_l, held)
+        head_name, head_ms, head_inc, head_tau = "cnn_only", ms_cnn, 100 * dj(j_l, held), None
     else:
         head_name, head_ms, head_inc = f"fallback_{int(chosen[0] * 100)}pct", chosen[1], chosen[2]
+        head_tau = taus[chosen[0]]
+    # end to end: regions from pinned host memory, the headline decision, labels back to the host
+    lab_h = torch.empty(labels_ex.shape, dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        regs.copy_(regs_p, non_blocking=True)
+        lab, mg = net.infer(regs, slots, margin=True)
+        if head_tau is not None:
+            idx, cnt = b.cnn_select(mg, head_tau)
+            search.search_subset(regs, qs, idx, cnt, lab)
+        lab_h.copy_(lab, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = gpx(e0.elapsed_time(e1) / reps)
     # roofline of the CNN inference kernel (tensor-core contraction)
     flop = (CNN_FLOP_PER_REGION + len(slots) * CNN_HEAD_FLOP_PER_SLOT) * n
     tflops = flop / (ms_cnn / 1e3) / 1e12
@@ -738,7 +754,10 @@ def run_learned(args):
                      "flop_per_region": CNN_FLOP_PER_REGION + len(slots) * CNN_HEAD_FLOP_PER_SLOT,
                      "peak_kind": kind},
         "cpu_baseline": None,
-        "gpu_launches": None, "clocks": clk,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(regs_p.numel() * 2),
+                "d2h_bytes_per_step": int(lab_h.numel())},
+        # the headline decision per step: inference (+ fallback pick + subset search)
+        "gpu_launches": reps * (1 if head_tau is None else 3), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -197,6 +197,8 @@ void fill_output(float* recon, int64_t pitch, int64_t bstride, int batch, BlockA
   a.out_pitch = pitch;
   a.out_bstride = batch > 1 ? bstride : 0;
   a.out_vec = aligned16(recon) && (pitch * 4) % 16 == 0 && (batch == 1 || (bstride * 4) % 16 == 0);
+  a.out_v8 = (reinterpret_cast<uintptr_t>(recon) & 31u) == 0 && (pitch * 4) % 32 == 0 &&
+             (batch == 1 || (bstride * 4) % 32 == 0);
 }
 
 // pipelined-kernel work units: segments of up to blocks_per_cta(n) blocks

@@ -20,6 +20,7 @@ struct BlockArgs {
   float* out;
   long long out_pitch, out_bstride;  // elements
   int out_vec;
+  int out_v8;                        // 1: rows 32-byte aligned, 256-bit stores allowed
   // coefficient buffer [img][by][bx][N][N] (forward output / inverse input)
   void* coeff;
   // zonal retention

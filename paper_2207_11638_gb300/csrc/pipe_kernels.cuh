@@ -238,10 +238,14 @@ __device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up
   const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
   if (up.fast) {
     float* orow = up.orow0 + static_cast<long long>(r) * up.out_pitch;
+    if (N == 8 && a.out_v8) {
+      stcs_v8(orow, rec);                    // the whole block row: one full sector per thread
+    } else {
 #pragma unroll
-    for (int c = 0; c < N / 4; ++c)
-      __stcs(reinterpret_cast<float4*>(orow + 4 * c),
-             make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2], rec[4 * c + 3]));
+      for (int c = 0; c < N / 4; ++c)
+        __stcs(reinterpret_cast<float4*>(orow + 4 * c),
+               make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2], rec[4 * c + 3]));
+    }
     if (a.partial == nullptr) return 0.f;
     float lo, hi;
     unpk2(row_error<N, InT>(row, rec2, pk2(0.f, 0.f)), lo, hi);

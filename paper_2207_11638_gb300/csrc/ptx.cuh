@@ -76,6 +76,13 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   return p;
 }
 
+// 256-bit streaming store of 8 floats (p 32-byte aligned): one full 32-byte sector per thread
+__device__ __forceinline__ void stcs_v8(float* p, const float* v) {
+  asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+
 __device__ __forceinline__ uint4 lds_v4(const void* p) {
   return *reinterpret_cast<const uint4*>(p);
 }
