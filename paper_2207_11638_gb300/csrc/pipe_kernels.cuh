@@ -279,11 +279,15 @@ __device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up
 // block is converted as in store_row but written to the warp's staging
 // buffer `obuf` (the exchange buffer, idle by then) instead of global
 // memory; the warp then writes whole image-row segments of its adjacent
-// blocks (copy_out).  Storing a block's rows straight from the threads that
-// own them makes every 128-bit store touch one cache line per lane.
+// blocks (copy_out).  For N = 32 copy_out also sums the squared error,
+// reading the staged input of the pixels it writes.  Storing a block's rows straight from the threads
+// that own them makes every 128-bit store touch one cache line per lane.
 //   N = 16: staging row pitch 128 floats (8 blocks x 16), chunk c of block b
 //           at physical chunk c ^ ((b >> 1) & 3) (conflict-free writes);
 //   N = 32: staging row pitch 68 floats (2 blocks x 32 + 4 pad).
+// N = 16 also returns the row's squared error against the staged input (its
+// 32-byte rows read with 128-bit loads: fewer loads than copy_out's 64-bit
+// ones); N = 32 leaves the error to copy_out and returns 0.
 template <int N, typename InT>
 __device__ __forceinline__ float stage_out_row(const BlockArgs& a, const unsigned char* stage, int lb, int r,
                                                const int (&x)[N], float* obuf, int lbw) {
@@ -302,33 +306,68 @@ __device__ __forceinline__ float stage_out_row(const BlockArgs& a, const unsigne
   for (int c = 0; c < N / 4; ++c)
     *reinterpret_cast<float4*>(orow + 4 * (c ^ swz)) = make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2],
                                                                    rec[4 * c + 3]);
-  if (a.partial == nullptr) return 0.f;
+  if (N != 16 || a.partial == nullptr) return 0.f;
   const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
   float lo, hi;
   unpk2(row_error<N, InT>(row, rec2, pk2(0.f, 0.f)), lo, hi);
   return lo + hi;
 }
 
+// squared error of 4 staged pixels (columns col .. col + 3 of staged row `row`) against 4 reconstructions
+template <typename InT>
+__device__ __forceinline__ f32x2 quad_error(const InT* row, int col, float4 rec, f32x2 acc2) {
+  const f32x2 neg1 = pk2(-1.f, -1.f);
+  f32x2 r0, r1;
+  if constexpr (sizeof(InT) == 2) {
+    const uint2 q = *reinterpret_cast<const uint2*>(row + col);
+    const f32x2 mg = pk2(-kMagicI16, -kMagicI16);
+    r0 = add2(pk2(i16lo_magic(q.x), i16hi_magic(q.x)), mg);
+    r1 = add2(pk2(i16lo_magic(q.y), i16hi_magic(q.y)), mg);
+  } else {
+    const uint32_t q = *reinterpret_cast<const uint32_t*>(row + col);
+    const f32x2 mg = pk2(-kMagicU8, -kMagicU8);
+    r0 = add2(pk2(u8_magic(q, 0), u8_magic(q, 1)), mg);
+    r1 = add2(pk2(u8_magic(q, 2), u8_magic(q, 3)), mg);
+  }
+  const f32x2 e0 = fma2(r0, neg1, pk2(rec.x, rec.y));
+  const f32x2 e1 = fma2(r1, neg1, pk2(rec.z, rec.w));
+  acc2 = fma2(e0, e0, acc2);
+  return fma2(e1, e1, acc2);
+}
+
 // Write the staged rows of the warp's blocks (N rows, each one contiguous
 // segment of 8 x 16 or 2 x 32 floats starting at `base`, the first block's
-// row 0) with 128-bit streaming stores that each cover whole cache lines.
-template <int N>
-__device__ __forceinline__ void copy_out(const float* obuf, float* base, long long pitch, int lane) {
+// row 0) with 128-bit streaming stores that each cover whole cache lines,
+// and return this lane's share of their squared error against the staged
+// input (`srow0`: the warp's first pixel of staged row 0) when `err`.
+template <int N, typename InT>
+__device__ __forceinline__ float copy_out(const float* obuf, float* base, long long pitch, int lane,
+                                          const unsigned char* stage, int lb0, bool err) {
+  typedef PipeGeo<N, InT> PG;
+  f32x2 acc2 = pk2(0.f, 0.f);
   if constexpr (N == 16) {
     const int b = lane >> 2, c = (lane & 3) ^ ((b >> 1) & 3);
+    const int col = lb0 * 16 + b * 16 + c * 4;
 #pragma unroll 4
-    for (int r = 0; r < 16; ++r)
-      __stcs(reinterpret_cast<float4*>(base + r * pitch + b * 16 + c * 4),
-             *reinterpret_cast<const float4*>(obuf + r * 128 + lane * 4));
+    for (int r = 0; r < 16; ++r) {
+      const float4 v = *reinterpret_cast<const float4*>(obuf + r * 128 + lane * 4);
+      __stcs(reinterpret_cast<float4*>(base + r * pitch + b * 16 + c * 4), v);
+      if (err) acc2 = quad_error<InT>(reinterpret_cast<const InT*>(stage + r * PG::ROWP), col, v, acc2);
+    }
   } else {
     const int h = lane >> 4, ch = lane & 15;
+    const int col = lb0 * 32 + ch * 4;
 #pragma unroll 4
     for (int k = 0; k < 16; ++k) {
       const int r = 2 * k + h;
-      __stcs(reinterpret_cast<float4*>(base + r * pitch + ch * 4),
-             *reinterpret_cast<const float4*>(obuf + r * 68 + ch * 4));
+      const float4 v = *reinterpret_cast<const float4*>(obuf + r * 68 + ch * 4);
+      __stcs(reinterpret_cast<float4*>(base + r * pitch + ch * 4), v);
+      if (err) acc2 = quad_error<InT>(reinterpret_cast<const InT*>(stage + r * PG::ROWP), col, v, acc2);
     }
   }
+  float lo, hi;
+  unpk2(acc2, lo, hi);
+  return lo + hi;
 }
 
 __device__ __forceinline__ float* warp_base(float* orow0, int src_lane) {
@@ -464,7 +503,7 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
         acc += stage_out_row<16, InT>(a, stage, lb, (k & 1) ? 15 - r0 : r0, xr[k], obuf, lbw);
       }
       __syncwarp();
-      copy_out<16>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane);
+      copy_out<16, InT>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane, stage, lb - lbw, false);
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -594,12 +633,13 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
       madd_join<16>(cc[0], cc[1], lo);             // horizontal unfold, second level
       madd_join<16>(cc[2], cc[3], hi);
       madd_join<32>(lo, hi, x);                    // first level
-      if (co) acc += stage_out_row<32, InT>(a, stage, lb, t == 0 ? p : 31 - p, x, obuf, lbw);
+      if (co) stage_out_row<32, InT>(a, stage, lb, t == 0 ? p : 31 - p, x, obuf, lbw);
       else acc += store_row<32, InT>(a, up, stage, lb, t == 0 ? p : 31 - p, x);
     }
     if (co) {
       __syncwarp();
-      copy_out<32>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane);
+      acc = copy_out<32, InT>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane, stage, lb - lbw,
+                              a.partial != nullptr);
     }
     __syncwarp();
     return acc;
