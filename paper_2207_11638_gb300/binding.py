@@ -609,3 +609,81 @@ class Cnn:
         g, loss = self.grad(regions, slots, labels, costs, mu, stream)
         self.adam(g, lr, stream=stream)
         return loss
+
+    def save(self, path: str, extra: dict | None = None) -> None:
+        """Write the training state (master weights, Adam m and v, step, and an optional
+        JSON-able ``extra`` such as the data order's seed) to a checkpoint file."""
+        torch = _torch()
+        torch.cuda.synchronize(self.params.device)
+        write_checkpoint(path, self.params.cpu().numpy(), self.m.cpu().numpy(), self.v.cpu().numpy(), self.step,
+                         extra or {})
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        """(Cnn, extra) restored from a checkpoint written by ``save``; training resumes
+        exactly where it stopped (the kernels are deterministic)."""
+        torch = _torch()
+        params, m, v, step, extra = read_checkpoint(path)
+        net = cls(torch.from_numpy(params).to(device))
+        net.m.copy_(torch.from_numpy(m))
+        net.v.copy_(torch.from_numpy(v))
+        net.step = step
+        return net, extra
+
+
+# ---- checkpoint files of the selector's training state ----------------------
+# Layout (little-endian): magic b"CDCTCNN1", uint32 version, uint32 parameter
+# count, int64 Adam step, uint32 length of a UTF-8 JSON "extra" block, then
+# the JSON, then params, m, v as float32 arrays, then a CRC-32 (zlib) of every
+# preceding byte.  A file with another magic, version or parameter count, a
+# wrong length or a wrong checksum is rejected.
+CKPT_MAGIC, CKPT_VERSION = b"CDCTCNN1", 1
+
+
+class CheckpointError(ValueError):
+    pass
+
+
+def write_checkpoint(path: str, params, m, v, step: int, extra: dict) -> None:
+    import json
+    import struct
+    import zlib
+
+    import numpy as np
+    blob = json.dumps(extra, sort_keys=True).encode()
+    arrays = [np.ascontiguousarray(a, dtype="<f4") for a in (params, m, v)]
+    if any(a.size != CNN_PARAMS for a in arrays):
+        raise CheckpointError("every array must hold CNN_PARAMS values")
+    body = (CKPT_MAGIC + struct.pack("<IIqI", CKPT_VERSION, CNN_PARAMS, int(step), len(blob)) + blob +
+            b"".join(a.tobytes() for a in arrays))
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write(body + struct.pack("<I", zlib.crc32(body) & 0xFFFFFFFF))
+    os.replace(tmp, path)
+
+
+def read_checkpoint(path: str):
+    """(params, m, v, step, extra) of a checkpoint file; raises CheckpointError if it is invalid."""
+    import json
+    import struct
+    import zlib
+
+    import numpy as np
+    with open(path, "rb") as f:
+        data = f.read()
+    head = len(CKPT_MAGIC) + struct.calcsize("<IIqI")
+    if len(data) < head + 4 or data[:len(CKPT_MAGIC)] != CKPT_MAGIC:
+        raise CheckpointError("not a selector checkpoint (magic)")
+    version, count, step, nblob = struct.unpack_from("<IIqI", data, len(CKPT_MAGIC))
+    if version != CKPT_VERSION or count != CNN_PARAMS:
+        raise CheckpointError(f"unsupported checkpoint version {version} or parameter count {count}")
+    if len(data) != head + nblob + 3 * 4 * count + 4:
+        raise CheckpointError("truncated or oversized checkpoint")
+    (crc,) = struct.unpack_from("<I", data, len(data) - 4)
+    if zlib.crc32(data[:-4]) & 0xFFFFFFFF != crc:
+        raise CheckpointError("checkpoint checksum mismatch")
+    extra = json.loads(data[head:head + nblob].decode())
+    off = head + nblob
+    arrs = [np.frombuffer(data, dtype="<f4", count=count, offset=off + k * 4 * count).astype(np.float32)
+            for k in range(3)]
+    return arrs[0], arrs[1], arrs[2], int(step), extra

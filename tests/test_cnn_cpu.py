@@ -4,6 +4,7 @@ are rejected before any launch."""
 import ctypes
 
 import numpy as np
+import pytest
 
 from oracle import cnn
 from paper_2207_11638_gb300 import binding as b
@@ -100,3 +101,23 @@ def test_ssim_argument_checks():
     assert lib.cdct_ssim(ctypes.byref(d), fake, 64, 64 * 48, fake, fake, 8, None) == b.CDCT_EINVAL
     assert lib.cdct_ssim(ctypes.byref(d), fake, 10, 64 * 48, fake, fake, 1 << 20, None) == b.CDCT_EINVAL
     assert lib.cdct_ssim(ctypes.byref(d), None, 64, 64 * 48, fake, fake, 1 << 20, None) == b.CDCT_EINVAL
+
+
+def test_checkpoint_roundtrip_and_rejections(tmp_path):
+    rng = np.random.default_rng(2)
+    params = synth.cnn_init_params(4)
+    m = rng.standard_normal(params.size).astype(np.float32)
+    v = rng.random(params.size).astype(np.float32)
+    path = str(tmp_path / "sel.ckpt")
+    b.write_checkpoint(path, params, m, v, 1234, {"data_seed": 40, "epoch": 3})
+    p2, m2, v2, step, extra = b.read_checkpoint(path)
+    assert np.array_equal(p2, params) and np.array_equal(m2, m) and np.array_equal(v2, v)
+    assert step == 1234 and extra == {"data_seed": 40, "epoch": 3}
+    raw = open(path, "rb").read()
+    for bad, why in ((raw[:-10], "truncated"), (raw[:100] + bytes([raw[100] ^ 1]) + raw[101:], "checksum"),
+                     (b"XXXXXXXX" + raw[8:], "magic")):
+        open(path, "wb").write(bad)
+        with pytest.raises(b.CheckpointError):
+            b.read_checkpoint(path)
+    with pytest.raises(b.CheckpointError):
+        b.write_checkpoint(path, params[:10], m, v, 1, {})

@@ -180,3 +180,31 @@ def test_training_on_rd_labels_reduces_the_loss():
     acc = float((pred == labels).float().mean())
     major = np.mean([np.bincount(lab[i], minlength=17).max() / lab.shape[1] for i in range(3)])
     print(f"training-set label accuracy {acc:.3f} (most frequent label per slot, averaged: {major:.3f})")
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    """Save the training state mid-run, resume it in a fresh selector: the weights after
+    the remaining steps equal those of the uninterrupted run bit for bit."""
+    regions = torch.from_numpy(synth.residual_regions_32(512, seed=15)).cuda()
+    qs, slots = (8, 16, 32), (0, 1, 2)
+    labels, costs = b.RdSearch("hat").search(regions, qs, costs=True)
+
+    def step(net, k):
+        i = k % 2
+        net.train_step(regions[i * 256:(i + 1) * 256], slots, labels[:, i * 256:(i + 1) * 256].contiguous(),
+                       lr=1e-3, costs=costs[:, i * 256:(i + 1) * 256].contiguous(), mu=10.0)
+
+    net = b.Cnn(torch.from_numpy(synth.cnn_init_params(3)).cuda())
+    for k in range(5):
+        step(net, k)
+    path = str(tmp_path / "selector.ckpt")
+    net.save(path, {"next_batch": 5})
+    for k in range(5, 10):
+        step(net, k)
+    torch.cuda.synchronize()
+    net2, extra = b.Cnn.load(path)
+    assert extra == {"next_batch": 5} and net2.step == 5
+    for k in range(extra["next_batch"], 10):
+        step(net2, k)
+    torch.cuda.synchronize()
+    assert torch.equal(net2.params, net.params) and torch.equal(net2.m, net.m) and torch.equal(net2.v, net.v)
