@@ -308,9 +308,11 @@ __global__ void __launch_bounds__(kRdThreads, 3) rd_kernel(const RdKernelArgs ka
           if (l - 1 != 0) need8 |= 1u << qi;
         }
       }
-      if (EVN != 32) need32 = 0;
-      if (EVN != 16) need16 = 0;
-      if (EVN != 8) need8 = 0;
+      // a region that uses this size for any step is coded at every step: all warps then
+      // run the same code as the search (a per-step skip made warps diverge and fetch-bound)
+      need32 = (EVN == 32 && need32) ? all : 0;
+      need16 = (EVN == 16 && need16) ? all : 0;
+      need8 = (EVN == 8 && need8) ? all : 0;
       if (EVN != 32 && (need16 | need8) == 0) continue;   // nothing of this size to add (warp-uniform)
     }
     if ((need32 | need16 | need8) != 0) {
