@@ -52,12 +52,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run every transform with its default pipeline schedule")
-    ap.add_argument("--workload", choices=("frames", "uneven", "rd", "learned"), default="frames",
+    ap.add_argument("--workload", choices=("frames", "uneven", "rd", "learned", "pipeline4k"), default="frames",
                     help="frames: 64 1080p 4:2:0 residual frames (default); uneven: 4096 u8 images of "
                          "log-uniform sizes in one persistent launch per pass, CUDA-graph replay; rd: "
                          "exhaustive RD quadtree search over 200k 32x32 residual regions at q = 8, 16, 32; "
                          "learned: train the CNN size selector on the search's labels, then time CNN-chosen "
-                         "quadtrees + coding against exhaustive search + coding on the same regions")
+                         "quadtrees + coding against exhaustive search + coding on the same regions; pipeline4k: "
+                         "the trained selector against the search on 64 3840x2160 4:2:0 residual frames")
     ap.add_argument("--epochs", type=int, default=16, help="learned workload: training epochs")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned workload: peak Adam learning rate")
     ap.add_argument("--mu", type=float, default=300.0, help="learned workload: weight of the RD-regret loss term")
@@ -607,32 +608,14 @@ def _j_float(words):
     return w[..., 1].astype(np.float64) * 2.0 ** 64 + w[..., 0].astype(np.float64)
 
 
-def run_learned(args):
-    """The learned size selector against the exhaustive search on the 32 x 32 region workload.
-
-    Untimed set-up: regions are generated, shuffled once on the host and
-    uploaded; the exhaustive search labels them and gives the 17 partition
-    costs (training targets and judge).  Timed, each with CUDA events:
-    training (the library's forward/backward/Adam kernels, epochs over the
-    first 90 % of the regions); then, over all regions at q = 8, 16, 32, the
-    size decision
-      exhaustive: the search;
-      learned:    the CNN alone, or the CNN -> pick the regions whose margin is
-                  below tau -> exhaustive search on those (tau from quantiles
-                  of the training regions' margins);
-    and the decision followed by coding the chosen quadtrees (cdct_rd_evaluate).
-    RD-cost increase and PSNR are measured on the held-out 10 % and on all.
-    The headline is the learned decision at the smallest fallback share that
-    keeps the held-out RD-cost increase within 1 %."""
+def train_selector(args, dev):
+    """Regions of the 32 x 32 workload (shuffled once on the host), the exhaustive
+    search's labels and costs, and a selector trained on the first 90 % of them
+    with the library's kernels (untimed set-up for the pipelines; the training
+    itself is timed with CUDA events)."""
     import torch
     from paper_2207_11638_gb300 import binding as b
     from paper_2207_11638_gb300 import synth
-
-    rank, world, local = dist_env()
-    if world > 1:
-        raise SystemExit("the learned workload runs on one GPU")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     qs, slots = (8, 16, 32), (0, 1, 2)
     n = args.regions
     t0 = time.time()
@@ -667,6 +650,40 @@ def run_learned(args):
     b.check_device()
     train_ms = s_ev.elapsed_time(e_ev)
     net.pack()
+    return dict(qs=qs, slots=slots, n=n, regs=regs, regs_p=regs_p, search=search, labels_ex=labels_ex, n_train=n_train,
+                net=net, losses=losses, train_ms=train_ms, total=total, B=B, gen_s=gen_s, stream=stream)
+
+
+def run_learned(args):
+    """The learned size selector against the exhaustive search on the 32 x 32 region workload.
+
+    Untimed set-up: regions are generated, shuffled once on the host and
+    uploaded; the exhaustive search labels them and gives the 17 partition
+    costs (training targets and judge).  Timed, each with CUDA events:
+    training (the library's forward/backward/Adam kernels, epochs over the
+    first 90 % of the regions); then, over all regions at q = 8, 16, 32, the
+    size decision
+      exhaustive: the search;
+      learned:    the CNN alone, or the CNN -> pick the regions whose margin is
+                  below tau -> exhaustive search on those (tau from quantiles
+                  of the training regions' margins);
+    and the decision followed by coding the chosen quadtrees (cdct_rd_evaluate).
+    RD-cost increase and PSNR are measured on the held-out 10 % and on all.
+    The headline is the learned decision at the smallest fallback share that
+    keeps the held-out RD-cost increase within 1 %."""
+    import torch
+    from paper_2207_11638_gb300 import binding as b
+    from paper_2207_11638_gb300 import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("the learned workload runs on one GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t = train_selector(args, dev)
+    qs, slots, n, regs, regs_p = t["qs"], t["slots"], t["n"], t["regs"], t["regs_p"]
+    search, labels_ex, n_train, net = t["search"], t["labels_ex"], t["n_train"], t["net"]
+    losses, train_ms, total, B, gen_s, stream = t["losses"], t["train_ms"], t["total"], t["B"], t["gen_s"], t["stream"]
 
     def timed(fn, reps):
         for _ in range(2):
@@ -835,6 +852,119 @@ def run_learned(args):
     return 0
 
 
+def run_pipeline4k(args):
+    """The full pipeline on 64 frames of 3840x2160 4:2:0 int16 residuals (AR(1),
+    rho ~ U[0.90, 0.97] per frame; 796 Mpx, 777 600 32 x 32 regions), which the
+    selector never saw: it is trained first on the 32 x 32 region workload
+    (train_selector).  Timed with CUDA events over the luma and chroma planes:
+    the exhaustive search, the CNN alone, the CNN with the low-margin fallback
+    (tau from the training regions' margins), and each decision followed by
+    coding the chosen quadtrees.  RD-cost increase and per-q PSNR cover every
+    region of the 4K batch."""
+    import torch
+    from paper_2207_11638_gb300 import binding as b
+    from paper_2207_11638_gb300 import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("the 4K pipeline workload runs on one GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t = train_selector(args, dev)
+    qs, slots, search, net, stream = t["qs"], t["slots"], t["search"], t["net"], t["stream"]
+    n_train = t["n_train"]
+    # fallback thresholds from the training regions' smallest margins
+    _, mtr = net.infer(t["regs"], slots, margin=True)
+    mmin = mtr[:, :n_train].min(dim=0).values.float()
+    fracs = (0.1, 0.25, 0.4, 0.5, 0.6)
+    taus = {f: float(torch.quantile(mmin, f)) for f in fracs}
+    del t
+    t0 = time.time()
+    luma_h, chroma_h = synth.residual_frames_420(64, 2160, 3840, seed=5, threads=16)
+    gen_s = time.time() - t0
+    planes = [torch.from_numpy(luma_h).to(dev), torch.from_numpy(chroma_h).to(dev)]
+    npix = int(luma_h.size + chroma_h.size)
+    reps = max(3, min(args.steps, 10))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(stream)
+        for _ in range(reps):
+            fn()
+        e_.record(stream)
+        torch.cuda.synchronize()
+        return s_.elapsed_time(e_) / reps
+
+    out = {}
+
+    def decide_ex():
+        out["lab"] = [search.search(pl_, qs) for pl_ in planes]
+
+    def decide_cnn(tau=None):
+        labs = []
+        for pl_ in planes:
+            lab, mg = net.infer(pl_, slots, margin=True)
+            if tau is not None:
+                idx, cnt = b.cnn_select(mg, tau)
+                search.search_subset(pl_, qs, idx, cnt, lab)
+            labs.append(lab)
+        out["lab"] = labs
+
+    def code():
+        out["ev"] = [search.evaluate(pl_, qs, lab) for pl_, lab in zip(planes, out["lab"])]
+
+    rows = {}
+    with ClockSampler(local) as clocks:
+        for name, fn in [("exhaustive_search", decide_ex), ("cnn_only", decide_cnn)] + \
+                        [(f"fallback_{int(f * 100)}pct", (lambda f=f: decide_cnn(taus[f]))) for f in fracs]:
+            ms_dec = timed(fn)
+            ms_full = timed(lambda: (fn(), code()))
+            j = np.concatenate([_j_float(ev[0]) for ev in out["ev"]], axis=1)
+            d = [_j_float(ev[1]).sum(axis=1) / 2.0 ** 44 for ev in out["ev"]]
+            rows[name] = {"decision_ms": ms_dec, "with_coding_ms": ms_full, "j": j, "sse": d}
+    clk = clocks.summary()
+    b.check_device()
+    j_ex = rows["exhaustive_search"]["j"]
+    gpx = lambda ms: npix / (ms / 1e3) / 1e9
+    report, chosen = {}, None
+    for name, r in rows.items():
+        inc = 100 * float(r["j"].sum() / j_ex.sum() - 1.0)
+        psnr = {pname: [round(10 * math.log10(255.0 ** 2 * pix / v), 3) for v in sse]
+                for pname, pix, sse in (("luma", luma_h.size, r["sse"][0]), ("chroma", chroma_h.size, r["sse"][1]))}
+        report[name] = {"decision_ms": round(r["decision_ms"], 3), "decision_Gpixel_s": round(gpx(r["decision_ms"]), 2),
+                        "with_coding_ms": round(r["with_coding_ms"], 3),
+                        "with_coding_Gpixel_s": round(gpx(r["with_coding_ms"]), 2),
+                        "rd_cost_increase_pct": round(inc, 3),
+                        "rd_cost_increase_pct_per_q": [round(100 * float(r["j"][i].sum() / j_ex[i].sum() - 1), 3)
+                                                       for i in range(len(qs))],
+                        "psnr_db_per_q": psnr}
+        if name.startswith("fallback") and chosen is None and inc <= 1.0:
+            chosen = name
+    head = chosen or "cnn_only"
+    ms_ex = rows["exhaustive_search"]["decision_ms"]
+    ms_h = rows[head]["decision_ms"]
+    line = {
+        "metric": "Gpixel/s learned quadtree decision vs exhaustive RD search, 64 frames 3840x2160 4:2:0, 3 q",
+        "value": gpx(ms_h), "unit": UNIT, "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": ms_h,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16/f32 (CNN), int32/int64/u128 (RD)", "data": "synthetic",
+        "config": {"workload": "64 frames 3840x2160 Y + 2 x 1920x1080 chroma int16 residuals (AR(1) frame pairs, "
+                               "rho ~ U[0.90, 0.97]); T^ 8/16/32, q in {8, 16, 32}, lambda = q^2/4; selector trained "
+                               "on the 200 000-region workload, not on these frames",
+                   "pixels": npix, "regions_per_q": int(sum(b.RdSearch.region_count(p_) for p_ in planes)),
+                   "generation_s": round(gen_s, 1), "headline": f"{head}: RD-cost increase "
+                   f"{report[head]['rd_cost_increase_pct']:.3f} %, {ms_ex / ms_h:.2f}x the exhaustive search",
+                   "l2": "frames 1.6 GB, larger than L2; no flush"},
+        "pipelines": report,
+        "cpu_baseline": None,
+        "gpu_launches": reps * 2 * (1 if head == "cnn_only" else 3), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -845,6 +975,8 @@ def main():
         return run_rd(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "pipeline4k":
+        return run_pipeline4k(args)
     return run_ours(args)
 
 
