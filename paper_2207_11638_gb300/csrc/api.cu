@@ -534,7 +534,8 @@ cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, in
     }
     prefix[i] = units;
     const long long nbx = (im.width + n - 1) / n, nby = (im.height + n - 1) / n;
-    units += nby * ((nbx + S - 1) / S);
+    const int pack = pack_rows(static_cast<int>(nbx), S);
+    units += pack > 1 ? (nby + pack - 1) / pack : nby * ((nbx + S - 1) / S);
     pixels += static_cast<long long>(im.width) * im.height;
   }
   prefix[n_images] = units;

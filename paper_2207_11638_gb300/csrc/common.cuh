@@ -140,6 +140,11 @@ int ssim_launch(const void* ref, int dtype, long long ref_pitch, long long ref_b
                 long long rec_pitch, long long rec_bstride, int width, int height, int batch, double* partial,
                 double* ssim, void* stream);
 
+// Block rows per work unit of a descriptor-table image `nbx` blocks wide (S
+// blocks per unit): narrow images (at most half a unit wide) pack whole block
+// rows into one unit so that the unit's lanes are not left idle.
+__host__ __device__ constexpr int pack_rows(int nbx, int S) { return nbx <= S / 2 ? S / nbx : 1; }
+
 // Zig-zag position of (i, j) in an n x n block (anti-diagonals in order;
 // row index falling on even diagonals, rising on odd ones).
 __host__ __device__ constexpr int zigzag_pos(int n, int i, int j) {

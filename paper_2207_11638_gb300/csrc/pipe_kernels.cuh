@@ -70,14 +70,14 @@ struct PipeGeo {
 template <int N, int STAGES>
 struct PipeOcc { static constexpr int value = (N == 8 || STAGES == 1) ? 4 : 3; };
 
-// Read row r (N pixels) of block lb from a staged unit with 128-bit shared
-// loads.  `valid` = number of valid pixels of this block's rows (N unless
+// Read row r (N pixels) of the block whose row 0 starts at `sblk` in a staged
+// unit (rows `spitch` bytes apart) with 128-bit shared loads.  `valid` = number of valid pixels of this block's rows (N unless
 // the block crosses the right image edge, where columns are clamped to the
 // last valid one).
 template <int N, typename InT>
-__device__ __forceinline__ void stage_read_row(const unsigned char* stage, int lb, int r, int valid, int (&x)[N]) {
-  typedef PipeGeo<N, InT> PG;
-  const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
+__device__ __forceinline__ void stage_read_row(const unsigned char* sblk, int spitch, int r, int valid,
+                                               int (&x)[N]) {
+  const InT* row = reinterpret_cast<const InT*>(sblk + r * spitch);
   if (valid < N) {
 #pragma unroll
     for (int j = 0; j < N; ++j) x[j] = static_cast<int>(row[min(j, valid - 1)]);
@@ -183,6 +183,9 @@ struct UnitPos {
   float* orow0;       // output row 0 of the block
   long long out_pitch;
   int height;
+  const unsigned char* sblk;   // the block's staged row 0
+  int spitch;                  // bytes between staged rows
+  bool wrow;                   // the warp's blocks are adjacent in one block row
 };
 
 // squared error of one staged row against a packed reconstruction row
@@ -224,9 +227,7 @@ __device__ __forceinline__ f32x2 row_error(const InT* row, const f32x2 (&rec2)[N
 // Store row r of the block's reconstruction (4Z in x) and return its squared
 // error against the staged input.  Interior blocks take the check-free path.
 template <int N, typename InT>
-__device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up, const unsigned char* stage,
-                                           int lb, int r, const int (&x)[N]) {
-  typedef PipeGeo<N, InT> PG;
+__device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up, int r, const int (&x)[N]) {
   const f32x2 sc2 = pk2(a.scale, a.scale);
   f32x2 rec2[N / 2];
 #pragma unroll
@@ -235,7 +236,7 @@ __device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up
   float rec[N];
 #pragma unroll
   for (int j = 0; j < N / 2; ++j) unpk2(rec2[j], rec[2 * j], rec[2 * j + 1]);
-  const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
+  const InT* row = reinterpret_cast<const InT*>(up.sblk + r * up.spitch);
   if (up.fast) {
     float* orow = up.orow0 + static_cast<long long>(r) * up.out_pitch;
     if (N == 8 && a.out_v8) {
@@ -289,9 +290,8 @@ __device__ __forceinline__ float store_row(const BlockArgs& a, const UnitPos& up
 // 32-byte rows read with 128-bit loads: fewer loads than copy_out's 64-bit
 // ones); N = 32 leaves the error to copy_out and returns 0.
 template <int N, typename InT>
-__device__ __forceinline__ float stage_out_row(const BlockArgs& a, const unsigned char* stage, int lb, int r,
-                                               const int (&x)[N], float* obuf, int lbw) {
-  typedef PipeGeo<N, InT> PG;
+__device__ __forceinline__ float stage_out_row(const BlockArgs& a, const UnitPos& up, int r, const int (&x)[N],
+                                               float* obuf, int lbw) {
   const f32x2 sc2 = pk2(a.scale, a.scale);
   f32x2 rec2[N / 2];
 #pragma unroll
@@ -307,7 +307,7 @@ __device__ __forceinline__ float stage_out_row(const BlockArgs& a, const unsigne
     *reinterpret_cast<float4*>(orow + 4 * (c ^ swz)) = make_float4(rec[4 * c], rec[4 * c + 1], rec[4 * c + 2],
                                                                    rec[4 * c + 3]);
   if (N != 16 || a.partial == nullptr) return 0.f;
-  const InT* row = reinterpret_cast<const InT*>(stage + r * PG::ROWP) + lb * N;
+  const InT* row = reinterpret_cast<const InT*>(up.sblk + r * up.spitch);
   float lo, hi;
   unpk2(row_error<N, InT>(row, rec2, pk2(0.f, 0.f)), lo, hi);
   return lo + hi;
@@ -339,30 +339,29 @@ __device__ __forceinline__ f32x2 quad_error(const InT* row, int col, float4 rec,
 // segment of 8 x 16 or 2 x 32 floats starting at `base`, the first block's
 // row 0) with 128-bit streaming stores that each cover whole cache lines,
 // and return this lane's share of their squared error against the staged
-// input (`srow0`: the warp's first pixel of staged row 0) when `err`.
+// input (`sblk0`: the warp's first block's staged row 0) when `err`.
 template <int N, typename InT>
 __device__ __forceinline__ float copy_out(const float* obuf, float* base, long long pitch, int lane,
-                                          const unsigned char* stage, int lb0, bool err) {
-  typedef PipeGeo<N, InT> PG;
+                                          const unsigned char* sblk0, int spitch, bool err) {
   f32x2 acc2 = pk2(0.f, 0.f);
   if constexpr (N == 16) {
     const int b = lane >> 2, c = (lane & 3) ^ ((b >> 1) & 3);
-    const int col = lb0 * 16 + b * 16 + c * 4;
+    const int col = b * 16 + c * 4;
 #pragma unroll 4
     for (int r = 0; r < 16; ++r) {
       const float4 v = *reinterpret_cast<const float4*>(obuf + r * 128 + lane * 4);
       __stcs(reinterpret_cast<float4*>(base + r * pitch + b * 16 + c * 4), v);
-      if (err) acc2 = quad_error<InT>(reinterpret_cast<const InT*>(stage + r * PG::ROWP), col, v, acc2);
+      if (err) acc2 = quad_error<InT>(reinterpret_cast<const InT*>(sblk0 + r * spitch), col, v, acc2);
     }
   } else {
     const int h = lane >> 4, ch = lane & 15;
-    const int col = lb0 * 32 + ch * 4;
+    const int col = ch * 4;
 #pragma unroll 4
     for (int k = 0; k < 16; ++k) {
       const int r = 2 * k + h;
       const float4 v = *reinterpret_cast<const float4*>(obuf + r * 68 + ch * 4);
       __stcs(reinterpret_cast<float4*>(base + r * pitch + ch * 4), v);
-      if (err) acc2 = quad_error<InT>(reinterpret_cast<const InT*>(stage + r * PG::ROWP), col, v, acc2);
+      if (err) acc2 = quad_error<InT>(reinterpret_cast<const InT*>(sblk0 + r * spitch), col, v, acc2);
     }
   }
   float lo, hi;
@@ -395,11 +394,11 @@ struct UnitBody<8, P, CONV, InT, RFIX> {
                                               int* /*xch*/, int /*lane*/, int lb, unsigned long long mask) {
     int v[8][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) stage_read_row<8, InT>(stage, lb, i, up.valid, v[i]);
+    for (int i = 0; i < 8; ++i) stage_read_row<8, InT>(up.sblk, up.spitch, i, up.valid, v[i]);
     core8<8, P, CONV, E, RFIX>(v, mask, kept_ptr(a, up), 0);
     float acc = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc += store_row<8, InT>(a, up, stage, lb, i, v[i]);
+    for (int i = 0; i < 8; ++i) acc += store_row<8, InT>(a, up, i, v[i]);
     return acc;
   }
 };
@@ -426,7 +425,7 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         int x[16];
-        stage_read_row<16, InT>(stage, lb, rows[t], up.valid, x);
+        stage_read_row<16, InT>(up.sblk, up.spitch, rows[t], up.valid, x);
         madd<16>(x, h[t][0], h[t][1]);                 // horizontal fold
       }
       // vertical fold: top row p = r0 + r3, top row 7-p = r1 + r2,
@@ -495,20 +494,20 @@ struct UnitBody<16, P, CONV, InT, RFIX> {
     }
     __syncwarp();                           // every unfold read of the exchange buffer is done
     float acc = 0.f;
-    if (__all_sync(0xffffffffu, up.fast)) {
+    if (up.wrow && __all_sync(0xffffffffu, up.fast)) {
       float* obuf = reinterpret_cast<float*>(xch);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int r0 = (k >> 1) == 0 ? p : 7 - p;
-        acc += stage_out_row<16, InT>(a, stage, lb, (k & 1) ? 15 - r0 : r0, xr[k], obuf, lbw);
+        acc += stage_out_row<16, InT>(a, up, (k & 1) ? 15 - r0 : r0, xr[k], obuf, lbw);
       }
       __syncwarp();
-      copy_out<16, InT>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane, stage, lb - lbw, false);
+      copy_out<16, InT>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane, nullptr, 0, false);
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int r0 = (k >> 1) == 0 ? p : 7 - p;
-        acc += store_row<16, InT>(a, up, stage, lb, (k & 1) ? 15 - r0 : r0, xr[k]);
+        acc += store_row<16, InT>(a, up, (k & 1) ? 15 - r0 : r0, xr[k]);
       }
     }
     __syncwarp();
@@ -538,7 +537,7 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         int x[32], lo[16], hi[16];
-        stage_read_row<32, InT>(stage, lb, t == 0 ? p : 31 - p, up.valid, x);
+        stage_read_row<32, InT>(up.sblk, up.spitch, t == 0 ? p : 31 - p, up.valid, x);
         madd<32>(x, lo, hi);                       // horizontal fold, first level
         madd<16>(lo, hc[t][0], hc[t][1]);          // second level: c = h*2 + a'
         madd<16>(hi, hc[t][2], hc[t][3]);
@@ -620,7 +619,7 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
     }
     __syncwarp();                                  // every unfold read of the exchange buffer is done
     float acc = 0.f;
-    const bool co = __all_sync(0xffffffffu, up.fast);
+    const bool co = up.wrow && __all_sync(0xffffffffu, up.fast);
     float* obuf = reinterpret_cast<float*>(xch);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -633,13 +632,13 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
       madd_join<16>(cc[0], cc[1], lo);             // horizontal unfold, second level
       madd_join<16>(cc[2], cc[3], hi);
       madd_join<32>(lo, hi, x);                    // first level
-      if (co) stage_out_row<32, InT>(a, stage, lb, t == 0 ? p : 31 - p, x, obuf, lbw);
-      else acc += store_row<32, InT>(a, up, stage, lb, t == 0 ? p : 31 - p, x);
+      if (co) stage_out_row<32, InT>(a, up, t == 0 ? p : 31 - p, x, obuf, lbw);
+      else acc += store_row<32, InT>(a, up, t == 0 ? p : 31 - p, x);
     }
     if (co) {
       __syncwarp();
-      acc = copy_out<32, InT>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane, stage, lb - lbw,
-                              a.partial != nullptr);
+      acc = copy_out<32, InT>(obuf, warp_base(up.orow0, 0), up.out_pitch, lane, up.sblk - lbw * 32 * sizeof(InT),
+                              up.spitch, a.partial != nullptr);
     }
     __syncwarp();
     return acc;
@@ -653,6 +652,7 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
 template <typename InT>
 struct UnitSrc {
   int img, by, seg;
+  int pack, rows;         // block rows per unit (1 unless packed) and those this unit covers
   const InT* in;          // first pixel of the image
   long long in_pitch;
   int width, height, nbx;
@@ -676,6 +676,8 @@ __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, Unit
     d.nbx = a.nbx;
     d.out = a.out + static_cast<long long>(d.img) * a.out_bstride;
     d.out_pitch = a.out_pitch;
+    d.pack = 1;
+    d.rows = 1;
   } else {
     // the image whose unit range contains u (unit_prefix is non-decreasing)
     int lo = 0, hi = pa.n_images - 1;
@@ -693,10 +695,18 @@ __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, Unit
     d.nbx = (d.width + N - 1) / N;
     d.out = im->recon;
     d.out_pitch = im->recon_pitch;
-    const int upr = (d.nbx + PG::S - 1) / PG::S;
     const int rem = static_cast<int>(static_cast<long long>(u) - __ldg(pa.unit_prefix + lo));
-    d.by = rem / upr;
-    d.seg = rem - d.by * upr;
+    d.pack = pack_rows(d.nbx, PG::S);
+    if (d.pack > 1) {                 // a narrow image: `pack` whole block rows per unit
+      d.by = rem * d.pack;
+      d.seg = 0;
+      d.rows = min(d.pack, (d.height + N - 1) / N - d.by);
+    } else {
+      const int upr = (d.nbx + PG::S - 1) / PG::S;
+      d.by = rem / upr;
+      d.seg = rem - d.by * upr;
+      d.rows = 1;
+    }
   }
 }
 
@@ -738,12 +748,25 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     decode_unit<N, InT, TABLE>(pa, static_cast<uint32_t>(u), d);
     const int x0 = d.seg * PG::WPX;
     const uint32_t bytes = static_cast<uint32_t>(min(PG::WPX, d.width - x0) * es);
-    if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes * N);
-    __syncwarp();
-    if (lane < N) {
-      const int gy = min(d.by * N + lane, d.height - 1);
-      const InT* src = d.in + static_cast<long long>(gy) * d.in_pitch + x0;
-      bulk_g2s(smem + s * PG::STAGE_BYTES + lane * PG::ROWP, src, bytes, &full[s], policy);
+    if (d.pack == 1) {
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes * N);
+      __syncwarp();
+      if (lane < N) {
+        const int gy = min(d.by * N + lane, d.height - 1);
+        const InT* src = d.in + static_cast<long long>(gy) * d.in_pitch + x0;
+        bulk_g2s(smem + s * PG::STAGE_BYTES + lane * PG::ROWP, src, bytes, &full[s], policy);
+      }
+    } else {
+      // packed narrow image: rows * N whole pixel rows, `bytes` apart (a multiple of 16);
+      // rows * N * bytes <= N * ROWB <= STAGE_BYTES since pack * nbx <= S
+      const int nr = d.rows * N;
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes * nr);
+      __syncwarp();
+      for (int j = lane; j < nr; j += 32) {
+        const int gy = min(d.by * N + j, d.height - 1);
+        const InT* src = d.in + static_cast<long long>(gy) * d.in_pitch;
+        bulk_g2s(smem + s * PG::STAGE_BYTES + j * bytes, src, bytes, &full[s], policy);
+      }
     }
   };
 
@@ -772,14 +795,30 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     decode_unit<N, InT, TABLE>(pa, static_cast<uint32_t>(u), d);
     UnitPos up;
     up.img = d.img;
-    up.by = d.by;
-    up.bx = d.seg * PG::S + lb;
-    up.active = up.bx < d.nbx;
+    up.out_pitch = d.out_pitch;
+    up.height = d.height;
+    if (d.pack == 1) {
+      up.by = d.by;
+      up.bx = d.seg * PG::S + lb;
+      up.active = up.bx < d.nbx;
+      up.sblk = stage + lb * N * es;
+      up.spitch = PG::ROWP;
+      up.wrow = true;
+    } else {
+      // packed: block lb is block (lb % nbx) of block row by + lb / nbx
+      const int k = lb / d.nbx;
+      up.by = d.by + k;
+      up.bx = lb - k * d.nbx;
+      up.active = k < d.rows;
+      up.spitch = d.width * es;
+      up.sblk = up.active ? stage + k * N * up.spitch + up.bx * N * es : stage;
+      const int wb = N == 16 ? 8 : (N == 32 ? 2 : 1);       // blocks per warp
+      const int lb0 = lb - (N == 16 ? (lane & 7) : (N == 32 ? (lane >> 4) : 0));
+      up.wrow = (lb0 % d.nbx) + wb <= d.nbx;
+    }
     up.valid = up.active ? min(N, d.width - up.bx * N) : N;
     up.fast = up.active && up.valid == N && a.out_vec && (up.by + 1) * N <= d.height;
     up.orow0 = d.out + static_cast<long long>(up.by) * N * d.out_pitch + up.bx * N;
-    up.out_pitch = d.out_pitch;
-    up.height = d.height;
 
     float acc = Body::run(a, up, stage, xch, lane, lb, mask);
 

@@ -35,8 +35,10 @@ def test_valid_batch_sizes():
     assert st == b.CDCT_OK
     tb, wb, px = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
     assert b.lib().cdct_batch_sizes(h, ctypes.byref(tb), ctypes.byref(wb), ctypes.byref(px)) == 0
-    # units: image 0: 5 block rows x 1 segment; image 1: 2 x ceil(130 / 128) = 4
-    assert wb.value == (5 + 4) * 4 * 8
+    # units: image 0 is 8 blocks wide (at most half of a 128-block unit), so its
+    # 5 block rows pack into one unit of up to 128 / 8 = 16 rows; image 1:
+    # 2 block rows x ceil(130 / 128) = 4 units
+    assert wb.value == (1 + 4) * 4 * 8
     assert px.value == 64 * 40 + 1040 * 9
     assert tb.value >= 2 * ctypes.sizeof(b.CdctBatchImage) + 3 * 8
     assert b.lib().cdct_batch_destroy(h) == 0
