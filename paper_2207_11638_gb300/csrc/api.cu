@@ -669,37 +669,6 @@ cdct_status cdct_rd_region_count(const cdct_image* in, int64_t* n_regions) {
   return CDCT_OK;
 }
 
-cdct_status cdct_rd_search(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q, int32_t kappa_num,
-                           int32_t kappa_log2_den, uint8_t* labels, uint64_t* partition_cost, void* stream) {
-  if (rd == nullptr) return fail(CDCT_EINVAL, "null rd handle");
-  int64_t n_regions = 0;
-  cdct_status st = cdct_rd_region_count(in, &n_regions);
-  if (st != CDCT_OK) return st;
-  if (q == nullptr || n_q < 1 || n_q > 4) return fail(CDCT_EINVAL, "n_q must be 1..4 with a host array q");
-  for (int k = 0; k < n_q; ++k)
-    if (q[k] < 1 || q[k] > 4096) return fail(CDCT_EINVAL, "quantiser steps must be in 1..4096");
-  if (kappa_num < 0 || kappa_num > 1024) return fail(CDCT_EINVAL, "kappa_num must be in 0..1024");
-  if (kappa_log2_den < 0 || kappa_log2_den > 44) return fail(CDCT_EINVAL, "kappa_log2_den must be in 0..44");
-  if (labels == nullptr) return fail(CDCT_EINVAL, "null labels pointer");
-  if (n_regions == 0) return CDCT_OK;
-  // lambda' = kappa_num q^2 2^(44 - kappa_log2_den) as a 128-bit integer
-  unsigned long long lo[4], hi[4];
-  for (int k = 0; k < n_q; ++k) {
-    const unsigned __int128 lam = static_cast<unsigned __int128>(static_cast<unsigned long long>(kappa_num) *
-                                                                 static_cast<unsigned long long>(q[k]) * q[k])
-                                  << (44 - kappa_log2_den);
-    lo[k] = static_cast<unsigned long long>(lam);
-    hi[k] = static_cast<unsigned long long>(lam >> 64);
-  }
-  DeviceInfo* di = nullptr;
-  int rc = device_info(&di);
-  if (rc) return cuda_fail(rc, "device query");
-  rc = launch_rd(rd->variant, in->dtype, in->data, in->pitch, in->batch_stride, in->width, in->height, in->batch,
-                 rd->tables, q, n_q, lo, hi, labels, reinterpret_cast<unsigned long long*>(partition_cost), di->sms,
-                 stream);
-  return rc ? cuda_fail(rc, "rd launch") : CDCT_OK;
-}
-
 namespace {
 // argument checks shared by the RD entry points; lambda' per step as 128-bit words
 cdct_status rd_common(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q, int32_t kappa_num,
@@ -722,6 +691,23 @@ cdct_status rd_common(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_
   return CDCT_OK;
 }
 }  // namespace
+
+cdct_status cdct_rd_search(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q, int32_t kappa_num,
+                           int32_t kappa_log2_den, uint8_t* labels, uint64_t* partition_cost, void* stream) {
+  int64_t n_regions = 0;
+  unsigned long long lo[4], hi[4];
+  cdct_status st = rd_common(rd, in, q, n_q, kappa_num, kappa_log2_den, &n_regions, lo, hi);
+  if (st != CDCT_OK) return st;
+  if (labels == nullptr) return fail(CDCT_EINVAL, "null labels pointer");
+  if (n_regions == 0) return CDCT_OK;
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return cuda_fail(rc, "device query");
+  rc = launch_rd(rd->variant, in->dtype, in->data, in->pitch, in->batch_stride, in->width, in->height, in->batch,
+                 rd->tables, q, n_q, lo, hi, labels, reinterpret_cast<unsigned long long*>(partition_cost), di->sms,
+                 stream);
+  return rc ? cuda_fail(rc, "rd launch") : CDCT_OK;
+}
 
 cdct_status cdct_rd_search_subset(cdct_rd rd, const cdct_image* in, const int32_t* q, int32_t n_q,
                                   int32_t kappa_num, int32_t kappa_log2_den, const int64_t* region_index,
