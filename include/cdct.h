@@ -166,8 +166,12 @@ cdct_status cdct_plan_set_tuning(cdct_plan plan, int stages, int ctas_per_sm);
  * A batch lists images of any sizes (device pointers; rows, widths and
  * pointers 16-byte aligned).  cdct_batch_create validates the list on the
  * host (an invalid descriptor returns CDCT_EINVAL naming the image) and
- * builds a descriptor table: the images and the prefix sums of their work
- * units.  The caller allocates `table_bytes` of device memory for it and
+ * builds a descriptor table: the images, the prefix sums of their work units
+ * and one 16-byte record per work unit (its image, block row and segment, so
+ * that the kernel decodes a unit with one load).  A work unit is up to
+ * 128 / P blocks of one block row (P = 1, 4, 16 threads per block for N = 8,
+ * 16, 32), or several whole block rows of an image at most half that wide.
+ * The caller allocates `table_bytes` of device memory for it and
  * uploads it once with cdct_batch_upload; cdct_batch_fzi then runs the fused
  * forward -> zonal(r) -> inverse (+ PSNR per image) over every image in one
  * persistent launch (plus one launch for the PSNRs), which can be captured

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/cdct.h"
 #include "butterfly.cuh"
@@ -48,8 +49,8 @@ struct cdct_batch_s {
   int dtype, n_images;
   long long total_units;
   long long total_pixels;
-  size_t table_bytes, prefix_offset;
-  std::string host_table;        // BatchImage[n], padding, int64 unit_prefix[n + 1]
+  size_t table_bytes, prefix_offset, map_offset;
+  std::string host_table;        // BatchImage[n], int64 unit_prefix[n + 1], UnitDesc[units] (16-byte aligned)
 };
 
 namespace {
@@ -503,11 +504,38 @@ cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, in
   if (n_images < 1) return fail(CDCT_EINVAL, "n_images must be >= 1");
   if (dtype != CDCT_U8 && dtype != CDCT_I16) return fail(CDCT_EINVAL, "bad dtype");
   static_assert(sizeof(BatchImage) == sizeof(cdct_batch_image), "descriptor layout");
+  static_assert(sizeof(UnitDesc) == 16, "unit descriptor layout");
   const int es = dtype == CDCT_I16 ? 2 : 1;
   const int n = plan->n, S = blocks_per_cta(n);
+  std::vector<long long> prefix;
+  try {
+    prefix.resize(static_cast<size_t>(n_images) + 1);
+  } catch (...) {
+    return fail(CDCT_ENOMEM, "batch table allocation failed");
+  }
+  long long units = 0, pixels = 0;
+  for (int i = 0; i < n_images; ++i) {
+    const cdct_batch_image& im = images[i];
+    const std::string where = "batch image " + std::to_string(i) + ": ";
+    if (im.data == nullptr || im.recon == nullptr) return fail(CDCT_EINVAL, where + "null pointer");
+    if (im.width < 1 || im.height < 1) return fail(CDCT_EINVAL, where + "width and height must be >= 1");
+    if (im.pitch < im.width || im.recon_pitch < im.width) return fail(CDCT_EINVAL, where + "pitch < width");
+    if (!aligned16(im.data) || !aligned16(im.recon) || (im.pitch * es) % 16 || (im.recon_pitch * 4) % 16 ||
+        (static_cast<long long>(im.width) * es) % 16)
+      return fail(CDCT_EINVAL, where + "pixels, rows and widths must be 16-byte aligned");
+    prefix[i] = units;
+    const long long nbx = (im.width + n - 1) / n, nby = (im.height + n - 1) / n;
+    const int pack = pack_rows(static_cast<int>(nbx), S);
+    units += pack > 1 ? (nby + pack - 1) / pack : nby * ((nbx + S - 1) / S);
+    pixels += static_cast<long long>(im.width) * im.height;
+  }
+  prefix[n_images] = units;
+  if (units * (kThreads / 32) >= (1ll << 31)) return fail(CDCT_EINVAL, "batch too large for one launch (2^31 work units)");
+  // table: descriptors, unit prefix sums, then one UnitDesc per work unit
   const size_t desc_bytes = sizeof(BatchImage) * static_cast<size_t>(n_images);
   const size_t prefix_offset = (desc_bytes + 15) / 16 * 16;
-  const size_t table_bytes = prefix_offset + sizeof(long long) * (static_cast<size_t>(n_images) + 1);
+  const size_t map_offset = (prefix_offset + sizeof(long long) * (static_cast<size_t>(n_images) + 1) + 15) / 16 * 16;
+  const size_t table_bytes = map_offset + sizeof(UnitDesc) * static_cast<size_t>(units);
   cdct_batch_s* b = new (std::nothrow) cdct_batch_s();
   if (b == nullptr) return fail(CDCT_ENOMEM, "batch allocation failed");
   try {
@@ -516,32 +544,24 @@ cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, in
     delete b;
     return fail(CDCT_ENOMEM, "batch table allocation failed");
   }
-  long long units = 0, pixels = 0;
-  long long* prefix = reinterpret_cast<long long*>(&b->host_table[prefix_offset]);
+  std::memcpy(&b->host_table[prefix_offset], prefix.data(), sizeof(long long) * prefix.size());
+  UnitDesc* map = reinterpret_cast<UnitDesc*>(&b->host_table[map_offset]);
   for (int i = 0; i < n_images; ++i) {
-    const cdct_batch_image& im = images[i];
-    const std::string where = "batch image " + std::to_string(i) + ": ";
-    cdct_status st = CDCT_OK;
-    if (im.data == nullptr || im.recon == nullptr) st = fail(CDCT_EINVAL, where + "null pointer");
-    else if (im.width < 1 || im.height < 1) st = fail(CDCT_EINVAL, where + "width and height must be >= 1");
-    else if (im.pitch < im.width || im.recon_pitch < im.width) st = fail(CDCT_EINVAL, where + "pitch < width");
-    else if (!aligned16(im.data) || !aligned16(im.recon) || (im.pitch * es) % 16 || (im.recon_pitch * 4) % 16 ||
-             (static_cast<long long>(im.width) * es) % 16)
-      st = fail(CDCT_EINVAL, where + "pixels, rows and widths must be 16-byte aligned");
-    if (st != CDCT_OK) {
-      delete b;
-      return st;
+    const int nbx = (images[i].width + n - 1) / n, nby = (images[i].height + n - 1) / n;
+    const int pack = pack_rows(nbx, S), upr = (nbx + S - 1) / S;
+    for (long long k = 0; k < prefix[i + 1] - prefix[i]; ++k) {
+      UnitDesc& m = map[prefix[i] + k];
+      m.img = i;
+      if (pack > 1) {
+        m.by = static_cast<int32_t>(k * pack);
+        m.seg = 0;
+        m.rows = std::min(pack, nby - m.by);
+      } else {
+        m.by = static_cast<int32_t>(k / upr);
+        m.seg = static_cast<int32_t>(k - static_cast<long long>(m.by) * upr);
+        m.rows = 1;
+      }
     }
-    prefix[i] = units;
-    const long long nbx = (im.width + n - 1) / n, nby = (im.height + n - 1) / n;
-    const int pack = pack_rows(static_cast<int>(nbx), S);
-    units += pack > 1 ? (nby + pack - 1) / pack : nby * ((nbx + S - 1) / S);
-    pixels += static_cast<long long>(im.width) * im.height;
-  }
-  prefix[n_images] = units;
-  if (units * (kThreads / 32) >= (1ll << 31)) {
-    delete b;
-    return fail(CDCT_EINVAL, "batch too large for one launch (2^31 work units)");
   }
   std::memcpy(&b->host_table[0], images, desc_bytes);
   b->plan = plan;
@@ -551,6 +571,7 @@ cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, in
   b->total_pixels = pixels;
   b->table_bytes = table_bytes;
   b->prefix_offset = prefix_offset;
+  b->map_offset = map_offset;
   *out = b;
   return CDCT_OK;
 }
@@ -607,6 +628,7 @@ cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, do
   pa.images = static_cast<const BatchImage*>(device_table);
   pa.unit_prefix = reinterpret_cast<const long long*>(static_cast<const char*>(device_table) + batch->prefix_offset);
   pa.n_images = batch->n_images;
+  pa.unit_map = reinterpret_cast<const UnitDesc*>(static_cast<const char*>(device_table) + batch->map_offset);
   rc = pipe_launch(plan->n, plan->variant, plan->conv, batch->dtype, pa, r, di->sms, plan->tuning, stream);
   if (rc) return cuda_fail(rc, "batch launch");
   if (psnr_db != nullptr) {

@@ -75,6 +75,13 @@ struct BatchImage {
   int64_t pitch, recon_pitch;  // elements
 };
 
+// One work unit of a descriptor-table batch, expanded on the host: its
+// image, first block row, segment of that row, and the block rows it covers
+// (more than one for a narrow image packed `pack_rows` rows per unit).
+struct alignas(16) UnitDesc {
+  int32_t img, by, seg, rows;
+};
+
 // Launch arguments of the persistent pipelined fused kernel.
 struct PipeArgs {
   BlockArgs b;
@@ -85,6 +92,7 @@ struct PipeArgs {
   // descriptor-table batches: images[i] and unit_prefix[i] = units before image i
   const BatchImage* images;
   const long long* unit_prefix;
+  const UnitDesc* unit_map;  // per work unit
   int n_images;
   int* err;                // device error word (bit 0: a bulk copy never landed)
   long long wait_limit;    // SM cycles before a stage wait gives up

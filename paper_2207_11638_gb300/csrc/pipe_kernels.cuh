@@ -679,15 +679,10 @@ __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, Unit
     d.pack = 1;
     d.rows = 1;
   } else {
-    // the image whose unit range contains u (unit_prefix is non-decreasing)
-    int lo = 0, hi = pa.n_images - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (__ldg(pa.unit_prefix + mid) <= static_cast<long long>(u)) lo = mid;
-      else hi = mid - 1;
-    }
-    const BatchImage* im = pa.images + lo;
-    d.img = lo;
+    // the unit's image, block row and segment, expanded on the host
+    const int4 m = __ldg(reinterpret_cast<const int4*>(pa.unit_map) + u);
+    const BatchImage* im = pa.images + m.x;
+    d.img = m.x;
     d.in = static_cast<const InT*>(im->data);
     d.in_pitch = im->pitch;
     d.width = im->width;
@@ -695,18 +690,10 @@ __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, Unit
     d.nbx = (d.width + N - 1) / N;
     d.out = im->recon;
     d.out_pitch = im->recon_pitch;
-    const int rem = static_cast<int>(static_cast<long long>(u) - __ldg(pa.unit_prefix + lo));
     d.pack = pack_rows(d.nbx, PG::S);
-    if (d.pack > 1) {                 // a narrow image: `pack` whole block rows per unit
-      d.by = rem * d.pack;
-      d.seg = 0;
-      d.rows = min(d.pack, (d.height + N - 1) / N - d.by);
-    } else {
-      const int upr = (d.nbx + PG::S - 1) / PG::S;
-      d.by = rem / upr;
-      d.seg = rem - d.by * upr;
-      d.rows = 1;
-    }
+    d.by = m.y;
+    d.seg = m.z;
+    d.rows = m.w;
   }
 }
 
@@ -723,6 +710,11 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
   int* xch_all = reinterpret_cast<int*>(smem + STAGES * PG::STAGE_BYTES);
   __shared__ __align__(8) uint64_t full[STAGES];
   __shared__ int done[STAGES];           // warps that finished the stage's current unit
+  // descriptor tables: the decoded unit of each stage, written by the warp
+  // that issues its copies before its arrival on full[s] (so it is visible
+  // once the stage is), which keeps the descriptor loads off the other warps'
+  // path; uniform batches decode with two fixed-point divisions instead
+  __shared__ UnitSrc<InT> usrc[TABLE ? STAGES : 1];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int* xch = xch_all + warp * PG::XCH_WARP_WORDS;
@@ -749,7 +741,10 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     const int x0 = d.seg * PG::WPX;
     const uint32_t bytes = static_cast<uint32_t>(min(PG::WPX, d.width - x0) * es);
     if (d.pack == 1) {
-      if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes * N);
+      if (lane == 0) {
+        if constexpr (TABLE) usrc[s] = d;
+        mbar_arrive_expect_tx(&full[s], bytes * N);
+      }
       __syncwarp();
       if (lane < N) {
         const int gy = min(d.by * N + lane, d.height - 1);
@@ -760,7 +755,10 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
       // packed narrow image: rows * N whole pixel rows, `bytes` apart (a multiple of 16);
       // rows * N * bytes <= N * ROWB <= STAGE_BYTES since pack * nbx <= S
       const int nr = d.rows * N;
-      if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes * nr);
+      if (lane == 0) {
+        if constexpr (TABLE) usrc[s] = d;
+        mbar_arrive_expect_tx(&full[s], bytes * nr);
+      }
       __syncwarp();
       for (int j = lane; j < nr; j += 32) {
         const int gy = min(d.by * N + j, d.height - 1);
@@ -792,7 +790,8 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     const unsigned char* stage = smem + s * PG::STAGE_BYTES;
 
     UnitSrc<InT> d;
-    decode_unit<N, InT, TABLE>(pa, static_cast<uint32_t>(u), d);
+    if constexpr (TABLE) d = usrc[s];
+    else decode_unit<N, InT, false>(pa, static_cast<uint32_t>(u), d);
     UnitPos up;
     up.img = d.img;
     up.out_pitch = d.out_pitch;
