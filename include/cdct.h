@@ -167,8 +167,9 @@ cdct_status cdct_plan_set_tuning(cdct_plan plan, int stages, int ctas_per_sm);
  * pointers 16-byte aligned).  cdct_batch_create validates the list on the
  * host (an invalid descriptor returns CDCT_EINVAL naming the image) and
  * builds a descriptor table: the images, the prefix sums of their work units
- * and one 16-byte record per work unit (its image, block row and segment, so
- * that the kernel decodes a unit with one load).  A work unit is up to
+ * and one 64-byte record per work unit (its image's pointers and geometry,
+ * block row and segment, so that the kernel decodes a unit from one bulk
+ * copy).  A work unit is up to
  * 128 / P blocks of one block row (P = 1, 4, 16 threads per block for N = 8,
  * 16, 32), or several whole block rows of an image at most half that wide.
  * The caller allocates `table_bytes` of device memory for it and

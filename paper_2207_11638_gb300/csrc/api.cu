@@ -504,7 +504,7 @@ cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, in
   if (n_images < 1) return fail(CDCT_EINVAL, "n_images must be >= 1");
   if (dtype != CDCT_U8 && dtype != CDCT_I16) return fail(CDCT_EINVAL, "bad dtype");
   static_assert(sizeof(BatchImage) == sizeof(cdct_batch_image), "descriptor layout");
-  static_assert(sizeof(UnitDesc) == 16, "unit descriptor layout");
+  static_assert(sizeof(UnitDesc) == 64, "unit descriptor layout");
   const int es = dtype == CDCT_I16 ? 2 : 1;
   const int n = plan->n, S = blocks_per_cta(n);
   std::vector<long long> prefix;
@@ -551,6 +551,12 @@ cdct_status cdct_batch_create(cdct_plan plan, const cdct_batch_image* images, in
     const int pack = pack_rows(nbx, S), upr = (nbx + S - 1) / S;
     for (long long k = 0; k < prefix[i + 1] - prefix[i]; ++k) {
       UnitDesc& m = map[prefix[i] + k];
+      m.data = images[i].data;
+      m.recon = images[i].recon;
+      m.pitch = images[i].pitch;
+      m.recon_pitch = images[i].recon_pitch;
+      m.width = images[i].width;
+      m.height = images[i].height;
       m.img = i;
       if (pack > 1) {
         m.by = static_cast<int32_t>(k * pack);

@@ -76,10 +76,15 @@ struct BatchImage {
 };
 
 // One work unit of a descriptor-table batch, expanded on the host: its
-// image, first block row, segment of that row, and the block rows it covers
-// (more than one for a narrow image packed `pack_rows` rows per unit).
+// image's geometry and pointers, its first block row, the segment of that
+// row, and the block rows it covers (more than one for a narrow image packed
+// `pack_rows` rows per unit).  64 bytes, so that one bulk copy moves it.
 struct alignas(16) UnitDesc {
-  int32_t img, by, seg, rows;
+  const void* data;        // first pixel of the image
+  float* recon;            // first reconstructed pixel
+  int64_t pitch, recon_pitch;
+  int32_t width, height, img, by;
+  int32_t seg, rows, pad0, pad1;
 };
 
 // Launch arguments of the persistent pipelined fused kernel.

@@ -660,6 +660,22 @@ struct UnitSrc {
   long long out_pitch;
 };
 
+template <int N, typename InT>
+__device__ __forceinline__ void decode_record(const UnitDesc& m, UnitSrc<InT>& d) {
+  d.img = m.img;
+  d.in = static_cast<const InT*>(m.data);
+  d.in_pitch = m.pitch;
+  d.width = m.width;
+  d.height = m.height;
+  d.nbx = (d.width + N - 1) / N;
+  d.out = m.recon;
+  d.out_pitch = m.recon_pitch;
+  d.pack = pack_rows(d.nbx, PipeGeo<N, InT>::S);
+  d.by = m.by;
+  d.seg = m.seg;
+  d.rows = m.rows;
+}
+
 template <int N, typename InT, bool TABLE>
 __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, UnitSrc<InT>& d) {
   typedef PipeGeo<N, InT> PG;
@@ -679,21 +695,8 @@ __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, Unit
     d.pack = 1;
     d.rows = 1;
   } else {
-    // the unit's image, block row and segment, expanded on the host
-    const int4 m = __ldg(reinterpret_cast<const int4*>(pa.unit_map) + u);
-    const BatchImage* im = pa.images + m.x;
-    d.img = m.x;
-    d.in = static_cast<const InT*>(im->data);
-    d.in_pitch = im->pitch;
-    d.width = im->width;
-    d.height = im->height;
-    d.nbx = (d.width + N - 1) / N;
-    d.out = im->recon;
-    d.out_pitch = im->recon_pitch;
-    d.pack = pack_rows(d.nbx, PG::S);
-    d.by = m.y;
-    d.seg = m.z;
-    d.rows = m.w;
+    // the unit's record, expanded on the host
+    decode_record<N, InT>(pa.unit_map[u], d);
   }
 }
 
@@ -710,11 +713,14 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
   int* xch_all = reinterpret_cast<int*>(smem + STAGES * PG::STAGE_BYTES);
   __shared__ __align__(8) uint64_t full[STAGES];
   __shared__ int done[STAGES];           // warps that finished the stage's current unit
-  // descriptor tables: the decoded unit of each stage, written by the warp
-  // that issues its copies before its arrival on full[s] (so it is visible
-  // once the stage is), which keeps the descriptor loads off the other warps'
-  // path; uniform batches decode with two fixed-point divisions instead
+  // Descriptor tables.  usrc[s]: the decoded unit of stage s, written by the
+  // warp that issues its copies before its arrival on full[s] (so it is
+  // visible once the stage is).  rec[s]: the record of the unit that stage s
+  // takes next, bulk-copied with the current unit's pixels (and counted by
+  // full[s]), so that the refill decodes from shared memory.  Uniform
+  // batches decode with two fixed-point divisions instead.
   __shared__ UnitSrc<InT> usrc[TABLE ? STAGES : 1];
+  __shared__ __align__(16) UnitDesc rec[TABLE ? STAGES : 1];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int* xch = xch_all + warp * PG::XCH_WARP_WORDS;
@@ -734,18 +740,20 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
   }
   __syncthreads();
 
-  // one whole warp issues the copies of unit u into stage s
-  auto issue = [&](long long u, int s) {
-    UnitSrc<InT> d;
-    decode_unit<N, InT, TABLE>(pa, static_cast<uint32_t>(u), d);
+  // one whole warp issues the copies of unit u, decoded into d, into stage s
+  auto issue = [&](long long u, int s, const UnitSrc<InT>& d) {
     const int x0 = d.seg * PG::WPX;
     const uint32_t bytes = static_cast<uint32_t>(min(PG::WPX, d.width - x0) * es);
+    // the record of the unit this stage takes after u
+    const long long un = u + STAGES * G_;
+    const uint32_t rec_bytes = (TABLE && un < pa.total_units) ? static_cast<uint32_t>(sizeof(UnitDesc)) : 0u;
     if (d.pack == 1) {
       if (lane == 0) {
         if constexpr (TABLE) usrc[s] = d;
-        mbar_arrive_expect_tx(&full[s], bytes * N);
+        mbar_arrive_expect_tx(&full[s], bytes * N + rec_bytes);
       }
       __syncwarp();
+      if (TABLE && lane == 31 && rec_bytes != 0) bulk_g2s(&rec[s], pa.unit_map + un, rec_bytes, &full[s], policy);
       if (lane < N) {
         const int gy = min(d.by * N + lane, d.height - 1);
         const InT* src = d.in + static_cast<long long>(gy) * d.in_pitch + x0;
@@ -757,9 +765,10 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
       const int nr = d.rows * N;
       if (lane == 0) {
         if constexpr (TABLE) usrc[s] = d;
-        mbar_arrive_expect_tx(&full[s], bytes * nr);
+        mbar_arrive_expect_tx(&full[s], bytes * nr + rec_bytes);
       }
       __syncwarp();
+      if (TABLE && lane == 31 && rec_bytes != 0) bulk_g2s(&rec[s], pa.unit_map + un, rec_bytes, &full[s], policy);
       for (int j = lane; j < nr; j += 32) {
         const int gy = min(d.by * N + j, d.height - 1);
         const InT* src = d.in + static_cast<long long>(gy) * d.in_pitch;
@@ -771,7 +780,11 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
   if (warp == 0) {
     for (int s = 0; s < STAGES; ++s) {
       const long long u = blockIdx.x + s * G_;
-      if (u < pa.total_units) issue(u, s);
+      if (u < pa.total_units) {
+        UnitSrc<InT> d;
+        decode_unit<N, InT, TABLE>(pa, static_cast<uint32_t>(u), d);
+        issue(u, s, d);
+      }
     }
   }
 
@@ -841,8 +854,11 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     if (last) {
       const long long un = u + STAGES * G_;
       if (un < pa.total_units) {
-        fence_proxy_async_smem();
-        issue(un, s);
+        UnitSrc<InT> dn;
+        if constexpr (TABLE) decode_record<N, InT>(rec[s], dn);   // landed with unit u
+        else decode_unit<N, InT, false>(pa, static_cast<uint32_t>(un), dn);
+        fence_proxy_async_smem();    // the warps' reads of the stage (and of rec[s]) before the copies
+        issue(un, s, dn);
       }
     }
   }

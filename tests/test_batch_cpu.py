@@ -41,9 +41,9 @@ def test_valid_batch_sizes():
     assert wb.value == (1 + 4) * 4 * 8
     assert px.value == 64 * 40 + 1040 * 9
     # table: 2 descriptors (80 B), 3 prefix sums (24 B) padded to 112 B, then
-    # one 16-byte record per work unit
+    # one 64-byte record per work unit
     assert ctypes.sizeof(b.CdctBatchImage) == 40
-    assert tb.value == 112 + (1 + 4) * 16
+    assert tb.value == 112 + (1 + 4) * 64
     assert b.lib().cdct_batch_destroy(h) == 0
 
 
