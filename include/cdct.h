@@ -196,6 +196,11 @@ cdct_status cdct_batch_sizes(cdct_batch batch, size_t* table_bytes, size_t* work
                              int64_t* total_pixels);
 /* Copy the table to device_table (16-byte aligned, table_bytes); synchronises `stream`. */
 cdct_status cdct_batch_upload(cdct_batch batch, void* device_table, void* stream);
+/* Host copy of work unit `unit`'s record (0 <= unit < the batch's work units):
+ * out = {image index, first block row, segment of that row (units of up to
+ * 128 / P blocks), block rows covered}.  Reads host memory only.
+ * CDCT_EINVAL for a null argument or a unit out of range. */
+cdct_status cdct_batch_unit(cdct_batch batch, int64_t unit, int32_t out[4]);
 /* psnr_db: device array of n_images doubles (NULL to skip, then no workspace is needed). */
 cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, double* psnr_db,
                            void* workspace, size_t workspace_bytes, void* stream);

@@ -25,7 +25,7 @@ EXPORTS = (
     "cdct_forward", "cdct_zonal", "cdct_inverse", "cdct_psnr", "cdct_fwd_zonal_inv",
     "cdct_matrix", "cdct_last_error", "cdct_version", "cdct_check_device",
     "cdct_fwd_zonal_inv_noalloc", "cdct_plan_set_tuning", "cdct_batch_create", "cdct_batch_destroy",
-    "cdct_batch_sizes", "cdct_batch_upload", "cdct_batch_fzi",
+    "cdct_batch_sizes", "cdct_batch_upload", "cdct_batch_unit", "cdct_batch_fzi",
     "cdct_rd_create", "cdct_rd_destroy", "cdct_rd_tables", "cdct_rd_region_count", "cdct_rd_search",
     "cdct_cnn_packed_bytes", "cdct_cnn_pack", "cdct_cnn_infer", "cdct_cnn_workspace_size", "cdct_cnn_grad",
     "cdct_cnn_adam", "cdct_rd_search_subset", "cdct_rd_evaluate", "cdct_cnn_select",
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cdct_batch_destroy": (ctypes.c_int, [vp]),
         "cdct_batch_sizes": (ctypes.c_int, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(i64)]),
         "cdct_batch_upload": (ctypes.c_int, [vp, vp, vp]),
+        "cdct_batch_unit": (ctypes.c_int, [vp, i64, ctypes.POINTER(i32)]),
         "cdct_batch_fzi": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, sz, vp]),
         "cdct_rd_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp)]),
         "cdct_rd_destroy": (ctypes.c_int, [vp]),

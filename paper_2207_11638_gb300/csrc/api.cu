@@ -595,6 +595,17 @@ cdct_status cdct_batch_sizes(cdct_batch batch, size_t* table_bytes, size_t* work
   return CDCT_OK;
 }
 
+cdct_status cdct_batch_unit(cdct_batch batch, int64_t unit, int32_t out[4]) {
+  if (batch == nullptr || out == nullptr) return fail(CDCT_EINVAL, "null argument");
+  if (unit < 0 || unit >= batch->total_units) return fail(CDCT_EINVAL, "unit out of range");
+  const UnitDesc* map = reinterpret_cast<const UnitDesc*>(batch->host_table.data() + batch->map_offset);
+  out[0] = map[unit].img;
+  out[1] = map[unit].by;
+  out[2] = map[unit].seg;
+  out[3] = map[unit].rows;
+  return CDCT_OK;
+}
+
 cdct_status cdct_batch_upload(cdct_batch batch, void* device_table, void* stream) {
   if (batch == nullptr || device_table == nullptr) return fail(CDCT_EINVAL, "null argument");
   if (!aligned16(device_table)) return fail(CDCT_EINVAL, "device_table must be 16-byte aligned");

@@ -100,3 +100,43 @@ def test_autotune_cache_roundtrip_and_corruption(tmp_path):
     cache[bad] = {"stages": 2, "ctas_per_sm": 0, "ms": 2.0}
     autotune.save_cache(cache, path)
     assert autotune.load_cache(path) == cache
+
+
+def batch_unit(h, u):
+    out = (ctypes.c_int32 * 4)()
+    st = b.lib().cdct_batch_unit(h, u, out)
+    return st, tuple(out)
+
+
+@pytest.mark.parametrize("n", (8, 16, 32))
+def test_unit_records_follow_the_packing_rule(n):
+    """The host expands a batch into one record per work unit: an image at
+    most half a unit wide (nbx <= S / 2, S = 128 / P blocks) packs S / nbx
+    whole block rows per unit (the last unit keeps the remainder); any other
+    image has one unit per block row and segment of S blocks, row-major."""
+    plan = b.Plan(n, "hat")
+    S = {8: 128, 16: 32, 32: 8}[n]
+    dims = [(64, 40), (1040, 9), (16, 200), (2048, 33), (n * S // 2, 70), (n * S // 2 + 16, 3), (512, 512)]
+    items = [(FAKE + 65536 * i, FAKE + 65536 * i, w, h, w, w) for i, (w, h) in enumerate(dims)]
+    st, h = create(plan, items)
+    assert st == b.CDCT_OK
+    want = []
+    for i, (w, hh) in enumerate(dims):
+        nbx, nby = -(-w // n), -(-hh // n)
+        if nbx <= S // 2:
+            k = S // nbx
+            want += [(i, by, 0, min(k, nby - by)) for by in range(0, nby, k)]
+        else:
+            want += [(i, by, seg, 1) for by in range(nby) for seg in range(-(-nbx // S))]
+    tb, wb, px = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+    assert b.lib().cdct_batch_sizes(h, ctypes.byref(tb), ctypes.byref(wb), ctypes.byref(px)) == 0
+    assert wb.value == len(want) * 4 * 8
+    got = []
+    for u in range(len(want)):
+        st, rec = batch_unit(h, u)
+        assert st == b.CDCT_OK
+        got.append(rec)
+    assert got == want
+    assert batch_unit(h, len(want))[0] == b.CDCT_EINVAL
+    assert batch_unit(h, -1)[0] == b.CDCT_EINVAL
+    assert b.lib().cdct_batch_destroy(h) == 0
