@@ -3,7 +3,10 @@
 //
 // Work unit.  One segment of up to S consecutive blocks of one block row of
 // one image, 8192 pixels when full (S = 128, 32, 8 for N = 8, 16, 32).  The
-// grid is persistent; CTA c takes units c, c + G, c + 2G, ...
+// grid is persistent; CTA c takes units c, c + G, c + 2G, ...  A uniform
+// batch decodes a unit index with two fixed-point divisions.  A descriptor
+// table (TABLE) gives each unit a 64-byte record, expanded on the host, which
+// travels to shared memory with the stage's previous unit.
 //
 // Pipeline.  The input rows of a unit are staged in shared memory by bulk
 // asynchronous copies (cp.async.bulk, one per pixel row, issued by one warp)
