@@ -168,6 +168,47 @@ def cpu_cores_used():
     return 1   # numpy integer matmul runs on one thread
 
 
+def oracle_images_sample(images, budget_s: float, passes):
+    """The oracle over whole images (u8 or int16), all passes, until the budget is spent."""
+    from oracle import pipeline as pl
+    from paper_2207_11638_gb300.workload import zonal_r
+    done_px, t0, k = 0, time.perf_counter(), 0
+    while k < len(images):
+        im = images[k]
+        for n, v in passes:
+            res = pl.fzi_integer(im[None], n, v, zonal_r(n))
+            pl.psnr_from_sse(pl.sse_integer(im, res["z"][0], n), n, im.size)
+            done_px += im.size
+        k += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done_px / dt / 1e9, k, dt
+
+
+def oracle_rd_sample(regions, qs, budget_s: float, variant: str = "hat"):
+    """The oracle's exhaustive RD decision (all q) over 32 x 32 regions until the budget is spent."""
+    from oracle import rd as ord_
+    t0, k = time.perf_counter(), 0
+    while k < len(regions):
+        ord_.rd_search(regions[k:k + 1], variant, qs)
+        k += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return k * 1024 / dt / 1e9, k, dt
+
+
+def rd_baseline(args, regions, qs, what):
+    """cpu_baseline of an RD decision line: the oracle search on a bounded sample of `regions`."""
+    if args.no_cpu_baseline:
+        return None
+    gpx, k, secs = oracle_rd_sample(regions, qs, args.cpu_seconds)
+    return {"value": gpx, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+            "sample": f"{k} regions of {what}, exhaustive search at {len(qs)} q ({secs:.1f} s, pure-Python "
+                      "integer oracle, 1 thread)"}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle on the same workload
 # ---------------------------------------------------------------------------
@@ -503,6 +544,12 @@ def run_uneven(args):
     achieved = 5 * px_step * args.steps / (ms / 1e3) / 1e9     # u8 in + f32 out
     ps = torch.cat([bt.psnr for bt, _, _ in batches]).cpu().numpy()
     assert np.all(np.isfinite(ps)) and ps.min() > 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        gpx_c, k, secs = oracle_images_sample(host, args.cpu_seconds, wl.PASSES)
+        cpu = {"value": gpx_c, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"the first {k} image(s) of the batch through all 6 passes ({secs:.1f} s, numpy int64 "
+                         "matrix products, 1 thread)"}
     line = {
         "metric": METRIC + " (uneven batch, CUDA graph)", "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -515,6 +562,7 @@ def run_uneven(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "whole graph (6 batch passes)",
                      "algorithmic_bytes_per_px": 5, "peak_kind": f"{peak_kind} copy bandwidth"},
+        "cpu_baseline": cpu,
         "autotune": tuned, "gpu_launches": 2 * len(wl.PASSES) * args.steps, "clocks": clocks.summary(),
     }
     print(json.dumps(line, default=float), flush=True)
@@ -596,7 +644,7 @@ def run_rd(args):
                      "frac": achieved / peak, "traffic": None, "kernel": "rd_kernel",
                      "ops_per_region": rd_ops_per_region("hat", len(qs)),
                      "peak_kind": "152 SMs x 128 INT32 lanes x sampled SM clock; ops = butterfly adds only"},
-        "cpu_baseline": None,
+        "cpu_baseline": rd_baseline(args, regs_h, qs, "the same region set"),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": npix * 2,
                 "d2h_bytes_per_step": int(labels.numel())},
         "gpu_launches": args.steps, "clocks": clk,
@@ -850,7 +898,8 @@ def run_learned(args):
                      "traffic": None, "kernel": "cnn_infer_kernel (fused conv trunk + FC head, mma.sync bf16)",
                      "flop_per_region": CNN_FLOP_PER_REGION + len(slots) * CNN_HEAD_FLOP_PER_SLOT,
                      "peak_kind": kind},
-        "cpu_baseline": None,
+        # the decision's oracle baseline: the exhaustive search the selector replaces
+        "cpu_baseline": rd_baseline(args, regs_p.numpy(), qs, "the same region set"),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(regs_p.numel() * 2),
                 "d2h_bytes_per_step": int(lab_h.numel())},
         # the headline decision per step: inference (+ fallback pick + subset search)
@@ -966,7 +1015,10 @@ def run_pipeline4k(args):
                    f"{report[head]['rd_cost_increase_pct']:.3f} %, {ms_ex / ms_h:.2f}x the exhaustive search",
                    "l2": "frames 1.6 GB, larger than L2; no flush"},
         "pipelines": report,
-        "cpu_baseline": None,
+        # the decision's oracle baseline: the exhaustive search on the first frame's top 32-row tiles
+        "cpu_baseline": rd_baseline(
+            args, np.ascontiguousarray(luma_h[0, :128].reshape(4, 32, 120, 32).transpose(0, 2, 1, 3)).reshape(-1, 32, 32),
+            qs, "the first 4K luma frame"),
         "gpu_launches": reps * 2 * (1 if head == "cnn_only" else 3), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
