@@ -642,14 +642,14 @@ cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, do
   pa.total_units = batch->total_units;
   pa.wait_limit = 1ll << 31;
   pa.err = di->err;
-  pa.images = static_cast<const BatchImage*>(device_table);
-  pa.unit_prefix = reinterpret_cast<const long long*>(static_cast<const char*>(device_table) + batch->prefix_offset);
-  pa.n_images = batch->n_images;
+  const BatchImage* images = static_cast<const BatchImage*>(device_table);
+  const long long* unit_prefix =
+      reinterpret_cast<const long long*>(static_cast<const char*>(device_table) + batch->prefix_offset);
   pa.unit_map = reinterpret_cast<const UnitDesc*>(static_cast<const char*>(device_table) + batch->map_offset);
   rc = pipe_launch(plan->n, plan->variant, plan->conv, batch->dtype, pa, r, di->sms, plan->tuning, stream);
   if (rc) return cuda_fail(rc, "batch launch");
   if (psnr_db != nullptr) {
-    rc = launch_finalize_table(a.partial, pa.unit_prefix, pa.images, batch->n_images, kThreads / 32, psnr_db, stream);
+    rc = launch_finalize_table(a.partial, unit_prefix, images, batch->n_images, kThreads / 32, psnr_db, stream);
     if (rc) return cuda_fail(rc, "batch psnr launch");
   }
   return CDCT_OK;

@@ -94,11 +94,7 @@ struct PipeArgs {
   long long units_per_img;
   long long total_units;   // < 2^31
   FastDiv div_img, div_row;
-  // descriptor-table batches: images[i] and unit_prefix[i] = units before image i
-  const BatchImage* images;
-  const long long* unit_prefix;
-  const UnitDesc* unit_map;  // per work unit
-  int n_images;
+  const UnitDesc* unit_map;  // descriptor-table batches: one record per work unit (null: uniform batch)
   int* err;                // device error word (bit 0: a bulk copy never landed)
   long long wait_limit;    // SM cycles before a stage wait gives up
 };

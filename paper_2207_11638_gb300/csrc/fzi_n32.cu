@@ -32,7 +32,7 @@ static int pipe_n32(int conv, const PipeArgs& pa, int r, int num_sms, PipeTuning
 
 int pipe_launch_n32(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, PipeTuning t,
                     void* stream) {
-  const bool table = pa.images != nullptr;
+  const bool table = pa.unit_map != nullptr;
   if (variant == 1) {
     if (dtype == 0)
       return table ? pipe_n32<ParamsTilde, uint8_t, true>(conv, pa, r, num_sms, t, stream)

@@ -31,7 +31,7 @@ static int pipe_n8(int conv, const PipeArgs& pa, int r, int num_sms, PipeTuning 
 
 int pipe_launch_n8(int variant, int conv, int dtype, const PipeArgs& pa, int r, int num_sms, PipeTuning t,
                     void* stream) {
-  const bool table = pa.images != nullptr;
+  const bool table = pa.unit_map != nullptr;
   if (variant == 1) {
     if (dtype == 0)
       return table ? pipe_n8<ParamsTilde, uint8_t, true>(conv, pa, r, num_sms, t, stream)
