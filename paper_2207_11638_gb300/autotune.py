@@ -2,16 +2,20 @@
 
 For a plan and a representative input it times each candidate schedule
 (staging depth of the shared-memory input ring, resident CTAs per SM) with
-CUDA events on the caller's stream, keeps the fastest, applies it to the
-plan and records it in a JSON cache keyed by GPU name, N, variant,
-convention, pixel type and r.  The schedule never changes results, only
-speed.  A missing, unreadable or corrupt cache file is treated as empty
-(and rewritten), never as an error.
+CUDA events on the caller's stream, in ROUNDS interleaved rounds, and keeps
+the candidate with the fastest median.  The kernel's default schedule is
+kept unless another is faster by more than MARGIN: candidates that differ by
+less than the timing noise would otherwise be picked at random from run to
+run.  The choice is applied to the plan and recorded in a JSON cache keyed
+by GPU name, N, variant, convention, pixel type and r.  The schedule never
+changes results, only speed.  A missing, unreadable or corrupt cache file is
+treated as empty (and rewritten), never as an error.
 """
 from __future__ import annotations
 
 import json
 import os
+import statistics
 import tempfile
 
 DEFAULT_CACHE = os.environ.get(
@@ -19,6 +23,20 @@ DEFAULT_CACHE = os.environ.get(
 
 # (stages, ctas_per_sm): 0 = the kernel's default / as many CTAs as fit
 CANDIDATES = ((0, 0), (1, 0), (2, 0), (3, 0), (0, 2), (0, 3))
+DEFAULT = (0, 0)
+ROUNDS = 3
+MARGIN = 0.01
+
+
+def choose(samples: dict, margin: float = MARGIN):
+    """(stages, ctas_per_sm, median ms) from {(stages, ctas_per_sm): [ms, ...]}:
+    the fastest median, unless the default schedule is within `margin` of it.
+    Equal medians go to the smaller (stages, ctas_per_sm)."""
+    med = {k: statistics.median(v) for k, v in samples.items() if v}
+    best = min(med, key=lambda k: (med[k], k))
+    if DEFAULT in med and med[DEFAULT] <= med[best] * (1.0 + margin):
+        best = DEFAULT
+    return best[0], best[1], med[best]
 
 
 def cache_key(gpu: str, n: int, variant: str, conv: str, dtype: str, r: int) -> str:
@@ -79,10 +97,13 @@ def tune(plan, img, r, path: str = DEFAULT_CACHE, candidates=CANDIDATES, force=F
         best = cache[key]
         plan.set_tuning(best["stages"], best["ctas_per_sm"])
         return best
-    results = [(time_config(plan, img, r, st, ct), st, ct) for st, ct in candidates]
-    ms, st, ct = min(results)
+    samples = {tuple(c): [] for c in candidates}
+    for _ in range(ROUNDS):                 # interleaved, so that drift hits every candidate alike
+        for st, ct in candidates:
+            samples[(st, ct)].append(time_config(plan, img, r, st, ct))
+    st, ct, ms = choose(samples)
     best = {"stages": st, "ctas_per_sm": ct, "ms": ms,
-            "tried": [{"stages": a, "ctas_per_sm": b, "ms": t} for t, a, b in results]}
+            "tried": [{"stages": a, "ctas_per_sm": b, "ms": statistics.median(t)} for (a, b), t in samples.items()]}
     plan.set_tuning(st, ct)
     cache[key] = best
     save_cache(cache, path)

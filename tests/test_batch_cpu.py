@@ -140,3 +140,13 @@ def test_unit_records_follow_the_packing_rule(n):
     assert batch_unit(h, len(want))[0] == b.CDCT_EINVAL
     assert batch_unit(h, -1)[0] == b.CDCT_EINVAL
     assert b.lib().cdct_batch_destroy(h) == 0
+
+
+def test_autotune_choice_keeps_the_default_within_the_noise():
+    near = {(0, 0): [1.00, 1.006, 1.005], (2, 0): [0.998, 1.0, 0.997], (0, 3): [1.3, 1.2, 1.25]}
+    assert autotune.choose(near)[:2] == (0, 0)          # 0.998 vs 1.005: within 1 %
+    clear = {(0, 0): [1.035, 1.04, 1.03], (2, 0): [1.0, 0.99, 1.01], (1, 0): [1.02, 1.0, 1.03]}
+    st, ct, ms = autotune.choose(clear)
+    assert (st, ct) == (2, 0) and ms == 1.0              # median, not the best single sample
+    tie = {(3, 0): [1.0], (2, 0): [1.0]}
+    assert autotune.choose(tie)[:2] == (2, 0)            # no default among them: the smaller key
