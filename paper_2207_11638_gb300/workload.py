@@ -35,7 +35,9 @@ def pixels(luma: np.ndarray, chroma: np.ndarray) -> int:
 class FrameStep:
     """Device buffers, plans and launches of one step over a resident batch."""
 
-    def __init__(self, luma_dev, chroma_dev, passes=PASSES, conv: str = "paper"):
+    def __init__(self, luma_dev, chroma_dev, passes=PASSES, conv: str = "paper", per_pass_outputs: bool = False):
+        """``per_pass_outputs``: every pass writes its own reconstruction buffers
+        (``recon_y_of[p]``, ``recon_c_of[p]``) instead of overwriting one pair."""
         import torch
         self.torch = torch
         self.luma, self.chroma = luma_dev, chroma_dev
@@ -44,6 +46,12 @@ class FrameStep:
         dev = luma_dev.device
         self.recon_y = torch.empty(luma_dev.shape, dtype=torch.float32, device=dev)
         self.recon_c = torch.empty(chroma_dev.shape, dtype=torch.float32, device=dev)
+        self.recon_y_of = {p: self.recon_y for p in passes}
+        self.recon_c_of = {p: self.recon_c for p in passes}
+        if per_pass_outputs:
+            for p in passes[1:]:
+                self.recon_y_of[p] = torch.empty_like(self.recon_y)
+                self.recon_c_of[p] = torch.empty_like(self.recon_c)
         self.psnr_y = {p: torch.empty(luma_dev.shape[0], dtype=torch.float64, device=dev) for p in passes}
         self.psnr_c = {p: torch.empty(chroma_dev.shape[0], dtype=torch.float64, device=dev) for p in passes}
         ws = max(max(self.plans[p].workspace_size(luma_dev), self.plans[p].workspace_size(chroma_dev))
@@ -54,13 +62,14 @@ class FrameStep:
     def launch_pass(self, p, stream=None):
         plan = self.plans[p]
         r = zonal_r(p[0])
-        plan.fwd_zonal_inv(self.luma, r, out=self.recon_y, psnr_out=self.psnr_y[p], workspace=self.ws,
+        plan.fwd_zonal_inv(self.luma, r, out=self.recon_y_of[p], psnr_out=self.psnr_y[p], workspace=self.ws,
                            stream=stream)
-        plan.fwd_zonal_inv(self.chroma, r, out=self.recon_c, psnr_out=self.psnr_c[p], workspace=self.ws,
+        plan.fwd_zonal_inv(self.chroma, r, out=self.recon_c_of[p], psnr_out=self.psnr_c[p], workspace=self.ws,
                            stream=stream)
 
-    def run(self, stream=None, events=None):
-        """One step.  ``events``: optional list receiving (start, end, npix) per fused pass."""
+    def run(self, stream=None, events=None, after_pass=None):
+        """One step.  ``events``: optional list receiving (start, end, npix) per fused pass.
+        ``after_pass(p)``: optional callback after each pass is enqueued."""
         for p in self.passes:
             if events is not None:
                 s = self.torch.cuda.Event(enable_timing=True)
@@ -71,6 +80,8 @@ class FrameStep:
                 events.append((s, e, p))
             else:
                 self.launch_pass(p, stream)
+            if after_pass is not None:
+                after_pass(p)
 
     # launches per step of the library's own kernels: fused + finalize, two planes, per pass
     @property

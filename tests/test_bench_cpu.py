@@ -81,3 +81,26 @@ def test_oracle_sample_helpers():
     img = np.random.default_rng(1).integers(0, 256, (64, 96)).astype(np.uint8)
     gpx, k, secs = bench.oracle_images_sample([img, img], 0.0, wl.PASSES)
     assert k == 1 and gpx > 0
+
+
+def test_nvml_summary_reports_reasons_and_load():
+    s = object.__new__(bench.NvmlSampler)
+    s.interval = 0.002
+    s.rows = [(345.0, 2070.0, 120.0, 0x1), (2070.0, 2070.0, 900.0, 0x0), (1890.0, 2070.0, 1400.0, 0x4),
+              (2070.0, 2070.0, 1000.0, 0x0)]
+    out = s.summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 4
+    assert out["samples_under_load"] == 3 and out["reasons"] == ["sw_power_cap"]
+    s.rows.append((1500.0, 2070.0, 1300.0, 0x40 | 0x8))
+    assert s.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+    s.rows = []
+    assert s.summary()["reasons"] == ["unavailable"]
+
+
+def test_all_core_oracle_baseline_states_its_cores():
+    frames = np.random.default_rng(2).integers(-255, 256, (3, 32, 48)).astype(np.int16)
+    gpx, n, secs = bench.oracle_pool_sample(frames, 0.0, 2)
+    assert gpx > 0 and n == 2
+    cpu = bench.frames_cpu_baseline(frames, 0.0)
+    assert cpu["cores"] == cpu["nproc"] == bench.host_cores() >= 1
+    assert cpu["single_core"]["cores"] == 1 and cpu["single_core"]["value"] > 0 and cpu["value"] > 0
