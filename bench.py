@@ -52,13 +52,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run every transform with its default pipeline schedule")
-    ap.add_argument("--workload", choices=("frames", "uneven", "rd", "learned", "pipeline4k"), default="frames",
+    ap.add_argument("--pass", dest="pass_", default="N32_hat",
+                    help="pass workload: the transform, N{8,16,32}_{tilde,hat}")
+    ap.add_argument("--workload", choices=("frames", "uneven", "rd", "learned", "pipeline4k", "pass"), default="frames",
                     help="frames: 64 1080p 4:2:0 residual frames (default); uneven: 4096 u8 images of "
                          "log-uniform sizes in one persistent launch per pass, CUDA-graph replay; rd: "
                          "exhaustive RD quadtree search over 200k 32x32 residual regions at q = 8, 16, 32; "
                          "learned: train the CNN size selector on the search's labels, then time CNN-chosen "
                          "quadtrees + coding against exhaustive search + coding on the same regions; pipeline4k: "
-                         "the trained selector against the search on 64 3840x2160 4:2:0 residual frames")
+                         "the trained selector against the search on 64 3840x2160 4:2:0 residual frames; pass: one "
+                         "fused pass (--pass) over the luma planes of --frames frames, a small case for profiling")
     ap.add_argument("--epochs", type=int, default=16, help="learned workload: training epochs")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned workload: peak Adam learning rate")
     ap.add_argument("--mu", type=float, default=300.0, help="learned workload: weight of the RD-regret loss term")
@@ -1197,6 +1200,46 @@ def run_pipeline4k(args):
     return 0
 
 
+def run_pass(args):
+    """One fused pass (fwd + zonal(r = N^2/4) + inv + PSNR) over the luma planes
+    of the frame workload, launched `warmup + steps` times: the small case the
+    kernel profiles in profiles/ capture (e.g. 16 frames, 33 Mpx, inputs and
+    outputs larger than L2)."""
+    import torch
+    from paper_2207_11638_gb300 import binding as b
+    from paper_2207_11638_gb300 import workload as wl
+
+    n = int(args.pass_.split("_")[0][1:])
+    variant = args.pass_.split("_")[1]
+    local = dist_env()[2]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    luma_h, _ = wl.host_batch(frames=args.frames)
+    luma = torch.from_numpy(luma_h).to(dev)
+    plan = b.Plan(n, variant)
+    out = torch.empty(luma.shape, dtype=torch.float32, device=dev)
+    ps = torch.empty(luma.shape[0], dtype=torch.float64, device=dev)
+    ws = torch.empty(plan.workspace_size(luma) // 8 + 1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.fwd_zonal_inv(luma, wl.zonal_r(n), out=out, psnr_out=ps, workspace=ws)
+    torch.cuda.synchronize()
+    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_.record(stream)
+    for _ in range(args.steps):
+        plan.fwd_zonal_inv(luma, wl.zonal_r(n), out=out, psnr_out=ps, workspace=ws)
+    e_.record(stream)
+    torch.cuda.synchronize()
+    b.check_device()
+    ms = s_.elapsed_time(e_) / args.steps
+    px = luma.numel()
+    print(json.dumps({"workload": f"pass {args.pass_} over {args.frames} luma planes 1920x1080 int16",
+                      "ms_per_call": ms, "Gpixel_s": px / (ms / 1e3) / 1e9,
+                      "GBs_algorithmic": BYTES_PER_PX * px / (ms / 1e3) / 1e9,
+                      "psnr0": float(ps[0].cpu())}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1209,6 +1252,8 @@ def main():
         return run_learned(args)
     if args.workload == "pipeline4k":
         return run_pipeline4k(args)
+    if args.workload == "pass":
+        return run_pass(args)
     return run_ours(args)
 
 

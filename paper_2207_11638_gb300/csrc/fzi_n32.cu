@@ -11,12 +11,19 @@ KernelSet kernels_n32(int variant, int conv, int dtype) {
   return conv == 0 ? kernel_set_int<32, ParamsHat, 0>(dtype) : kernel_set_int<32, ParamsHat, 1>(dtype);
 }
 
-// Pipelined fused kernel.  Compile-time r for the paper convention at r in
-// {256} with the default staging depth (2); the alternative depths (1: four
-// resident CTAs per SM, 3) have r = 256; any other r, and the transpose convention, use the runtime
-// mask.  Descriptor-table batches use the default depth.
+// Pipelined fused kernel.  The paper convention at r = 256 (= N^2 / 4) without
+// kept-coefficient output runs the separable packed body (stage depth 1 by
+// default, or 2); other r, the transpose convention and kept output run the
+// fold + core body: compile-time r = 256 at depths 1-3 (default 2), the
+// runtime mask otherwise.  Descriptor-table batches use the default depths.
 template <class P, typename InT, bool TABLE>
 static int pipe_n32(int conv, const PipeArgs& pa, int r, int num_sms, PipeTuning t, void* stream) {
+  int rc = 0;
+  if (TABLE || t.stages != 2) {
+    if (pipe_try_sep<32, P, InT, 256, 1, TABLE>(pa, conv, r, num_sms, t.ctas_per_sm, stream, rc)) return rc;
+  } else {
+    if (pipe_try_sep<32, P, InT, 256, 2, false>(pa, conv, r, num_sms, t.ctas_per_sm, stream, rc)) return rc;
+  }
   const int stages = t.stages == 0 ? 2 : t.stages;
   if (conv == 0) {
     if constexpr (TABLE) {

@@ -70,8 +70,8 @@ struct PipeGeo {
 // resident CTAs per SM the register allocation is sized for (N = 16 / 32
 // with a one-stage ring fit four CTAs in shared memory, so they are built
 // for four)
-template <int N, int STAGES>
-struct PipeOcc { static constexpr int value = (N == 8 || STAGES == 1) ? 4 : 3; };
+template <int N, int STAGES, int BODY = 0>
+struct PipeOcc { static constexpr int value = (N == 8 || STAGES == 1 || BODY == 1) ? 4 : 3; };
 
 // Read row r (N pixels) of the block whose row 0 starts at `sblk` in a staged
 // unit (rows `spitch` bytes apart) with 128-bit shared loads.  `valid` = number of valid pixels of this block's rows (N unless
@@ -189,6 +189,8 @@ struct UnitPos {
   const unsigned char* sblk;   // the block's staged row 0
   int spitch;                  // bytes between staged rows
   bool wrow;                   // the warp's blocks are adjacent in one block row
+  const unsigned char* grow0;  // the block's input row 0 in global memory
+  long long gpitch;            // bytes between input rows
 };
 
 // squared error of one staged row against a packed reconstruction row
@@ -648,6 +650,58 @@ struct UnitBody<32, P, CONV, InT, RFIX> {
   }
 };
 
+}  // namespace cdct
+
+#include "sep_body.cuh"
+
+namespace cdct {
+
+// The fold + 8 x 8 core bodies behind the interface the kernel uses:
+// exchange words per warp, a constant area in shared memory (none), a
+// per-thread context (the zonal mask of the thread's sub-block) and run().
+template <int N, class P, int CONV, typename InT, int RFIX>
+struct FoldBody {
+  typedef UnitBody<N, P, CONV, InT, RFIX> B;
+  static constexpr int XCH_WARP_WORDS = PipeGeo<N, InT>::XCH_WARP_WORDS;
+  static constexpr int CONST_WORDS = 0;
+  struct Ctx {
+    unsigned long long mask;
+  };
+  static __device__ __forceinline__ void init_const(float*, int) {}
+  static __device__ __forceinline__ void init(Ctx& c, const BlockArgs& a, int lane, const float*) {
+    c.mask = a.slab_mask[B::sub_block(lane)];
+  }
+  static constexpr bool EARLY_RELEASE = false;
+  template <class Rel>
+  static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, int* xch, const float*, int lane,
+                                              const Ctx& cx, Rel&& release) {
+    const float acc = B::run(a, up, nullptr, xch, lane, 0, cx.mask);
+    release();                                  // the stage is read to the end (squared error)
+    return acc;
+  }
+};
+
+// BODY 0: fold + 8 x 8 core (any r, both conventions, kept coefficients);
+// BODY 1: separable packed passes (N = 16, 32; paper convention; r = RFIX).
+template <int N, class P, int CONV, typename InT, int RFIX, int BODY>
+struct BodySel {
+  typedef FoldBody<N, P, CONV, InT, RFIX> type;
+};
+template <class P, typename InT, int RFIX>
+struct BodySel<32, P, 0, InT, RFIX, 1> {
+  typedef SepBody32<P, InT, RFIX> type;
+};
+template <class P, typename InT, int RFIX>
+struct BodySel<16, P, 0, InT, RFIX, 1> {
+  typedef SepBody16<P, InT, RFIX> type;
+};
+
+template <int N, typename InT, class Body>
+constexpr size_t pipe_smem_bytes(int stages) {
+  return static_cast<size_t>(stages) * PipeGeo<N, InT>::STAGE_BYTES +
+         static_cast<size_t>(Body::XCH_WARP_WORDS * (kThreads / 32) + Body::CONST_WORDS) * 4;
+}
+
 // ---------------------------------------------------------------------------
 // Unit decoding: image, block row and segment of unit u, with the image's
 // geometry, for a uniform batch (BlockArgs) or a descriptor table.
@@ -706,14 +760,16 @@ __device__ __forceinline__ void decode_unit(const PipeArgs& pa, uint32_t u, Unit
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
-template <int N, class P, int CONV, typename InT, int RFIX, int STAGES, bool TABLE>
-__global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_kernel(const PipeArgs pa) {
+template <int N, class P, int CONV, typename InT, int RFIX, int STAGES, bool TABLE, int BODY>
+__global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES, BODY>::value) fzi_pipe_kernel(const PipeArgs pa) {
   typedef PipeGeo<N, InT> PG;
+  typedef typename BodySel<N, P, CONV, InT, RFIX, BODY>::type Body;
   constexpr int NW = kThreads / 32;
   const BlockArgs& a = pa.b;
 
   extern __shared__ __align__(128) unsigned char smem[];
   int* xch_all = reinterpret_cast<int*>(smem + STAGES * PG::STAGE_BYTES);
+  float* cbuf = reinterpret_cast<float*>(xch_all + Body::XCH_WARP_WORDS * NW);
   __shared__ __align__(8) uint64_t full[STAGES];
   __shared__ int done[STAGES];           // warps that finished the stage's current unit
   // Descriptor tables.  usrc[s]: the decoded unit of stage s, written by the
@@ -726,10 +782,13 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
   __shared__ __align__(16) UnitDesc rec[TABLE ? STAGES : 1];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int* xch = xch_all + warp * PG::XCH_WARP_WORDS;
+  int* xch = xch_all + warp * Body::XCH_WARP_WORDS;
   // block of this thread within the unit
   const int lb = (N == 8) ? tid : (N == 16 ? warp * 8 + (lane & 7) : warp * 2 + (lane >> 4));
-  const uint64_t policy = policy_evict_first();
+  // input lines are read once (evict first), or a second time from L2 by a
+  // body that releases its stage early and reads the pixels it compares with
+  // from global memory (normal priority)
+  const uint64_t policy = Body::EARLY_RELEASE ? policy_evict_normal() : policy_evict_first();
   const long long G_ = gridDim.x;
   const int es = static_cast<int>(sizeof(InT));
 
@@ -741,6 +800,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     }
     fence_mbar_init();
   }
+  Body::init_const(cbuf, tid);
   __syncthreads();
 
   // one whole warp issues the copies of unit u, decoded into d, into stage s
@@ -791,9 +851,9 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     }
   }
 
-  // the thread's sub-block, hence its zonal mask, is the same in every unit
-  typedef UnitBody<N, P, CONV, InT, RFIX> Body;
-  const unsigned long long mask = a.slab_mask[Body::sub_block(lane)];
+  // the thread's part of a unit (and so its zonal mask or factors) is the same in every unit
+  typename Body::Ctx ctx;
+  Body::init(ctx, a, lane, cbuf);
 
   bool failed = false;
   int it = 0;
@@ -834,35 +894,40 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
     up.valid = up.active ? min(N, d.width - up.bx * N) : N;
     up.fast = up.active && up.valid == N && a.out_vec && (up.by + 1) * N <= d.height;
     up.orow0 = d.out + static_cast<long long>(up.by) * N * d.out_pitch + up.bx * N;
+    up.gpitch = d.in_pitch * es;
+    up.grow0 = reinterpret_cast<const unsigned char*>(d.in + static_cast<long long>(up.by) * N * d.in_pitch + up.bx * N);
 
-    float acc = Body::run(a, up, stage, xch, lane, lb, mask);
+    // release the stage (the body calls this once it has read the stage for
+    // the last time); the last warp to do so refills it with unit u + STAGES*G
+    auto release = [&]() {
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) {
+        __threadfence_block();                 // this warp's reads of the stage come first
+        last = atomicAdd(&done[s], 1) == NW - 1;
+        if (last) {
+          done[s] = 0;
+          __threadfence_block();
+        }
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        const long long un = u + STAGES * G_;
+        if (un < pa.total_units) {
+          UnitSrc<InT> dn;
+          if constexpr (TABLE) decode_record<N, InT>(rec[s], dn);   // landed with unit u
+          else decode_unit<N, InT, false>(pa, static_cast<uint32_t>(un), dn);
+          fence_proxy_async_smem();    // the warps' reads of the stage (and of rec[s]) before the copies
+          issue(un, s, dn);
+        }
+      }
+    };
+    float acc = Body::run(a, up, xch, cbuf, lane, ctx, release);
 
     if (a.partial != nullptr) {
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
       if (lane == 0) a.partial[u * NW + warp] = static_cast<double>(acc);
-    }
-    // release the stage; the last warp to do so refills it with unit u + STAGES*G
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) {
-      __threadfence_block();                 // this warp's reads of the stage come first
-      last = atomicAdd(&done[s], 1) == NW - 1;
-      if (last) {
-        done[s] = 0;
-        __threadfence_block();
-      }
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      const long long un = u + STAGES * G_;
-      if (un < pa.total_units) {
-        UnitSrc<InT> dn;
-        if constexpr (TABLE) decode_record<N, InT>(rec[s], dn);   // landed with unit u
-        else decode_unit<N, InT, false>(pa, static_cast<uint32_t>(un), dn);
-        fence_proxy_async_smem();    // the warps' reads of the stage (and of rec[s]) before the copies
-        issue(un, s, dn);
-      }
     }
   }
 
@@ -879,11 +944,11 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES>::value) fzi_pipe_
   }
 }
 
-template <int N, class P, int CONV, typename InT, int RFIX, int STAGES, bool TABLE>
+template <int N, class P, int CONV, typename InT, int RFIX, int STAGES, bool TABLE, int BODY = 0>
 int launch_pipe(const PipeArgs& pa, int num_sms, int ctas_per_sm, void* stream) {
-  typedef PipeGeo<N, InT> PG;
-  auto kern = fzi_pipe_kernel<N, P, CONV, InT, RFIX, STAGES, TABLE>;
-  const size_t smem = PG::smem_bytes(STAGES);
+  typedef typename BodySel<N, P, CONV, InT, RFIX, BODY>::type Body;
+  auto kern = fzi_pipe_kernel<N, P, CONV, InT, RFIX, STAGES, TABLE, BODY>;
+  const size_t smem = pipe_smem_bytes<N, InT, Body>(STAGES);
   static int occ = -1;   // resident CTAs per SM (same for every GPU this library targets)
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -913,6 +978,15 @@ template <int N, class P, int CONV, typename InT, int STAGES, bool TABLE, int R0
 int pipe_launch_r(const PipeArgs& pa, int r, int num_sms, int ctas_per_sm, void* stream) {
   if (r != R0) return pipe_launch_r<N, P, CONV, InT, STAGES, TABLE, Rs...>(pa, r, num_sms, ctas_per_sm, stream);
   return launch_pipe<N, P, CONV, InT, R0, STAGES, TABLE>(pa, num_sms, ctas_per_sm, stream);
+}
+
+// The separable packed body where it applies (paper convention, r = RFIX,
+// no kept-coefficient output), else the fold + core body at its own depth.
+template <int N, class P, typename InT, int RFIX, int STAGES, bool TABLE>
+bool pipe_try_sep(const PipeArgs& pa, int conv, int r, int num_sms, int ctas_per_sm, void* stream, int& rc) {
+  if (conv != 0 || r != RFIX || pa.b.kept != nullptr) return false;
+  rc = launch_pipe<N, P, 0, InT, RFIX, STAGES, TABLE, 1>(pa, num_sms, ctas_per_sm, stream);
+  return true;
 }
 
 }  // namespace cdct

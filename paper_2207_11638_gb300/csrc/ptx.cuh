@@ -75,6 +75,12 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
+// L2 policy of ordinary priority (data read again shortly after)
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 
 // 256-bit streaming store of 8 floats (p 32-byte aligned): one full 32-byte sector per thread
 __device__ __forceinline__ void stcs_v8(float* p, const float* v) {

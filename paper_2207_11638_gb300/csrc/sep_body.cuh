@@ -1,0 +1,564 @@
+// Separable packed unit bodies of the persistent fused kernel, N = 16 and 32,
+// for the paper convention (Sec. 5.1: Y = T A U, Z = U Ym T) at a compile-time
+// zonal r.
+//
+// The 2-D transform runs as four 1-D passes over each N x N block, taken
+// from the paper's fast algorithms (Eqs. 3-7 and the JAM recursion of
+// Sec. 6, Eq. app_N; Jam<> in butterfly.cuh), in this order:
+//   A  X  = T A          column pass   16-bit lanes, two columns per 32-bit word
+//   B  2Y = X W          row pass      float pairs, two rows per lane
+//      Ym = zonal mask of 2Y
+//      Q  = 2Ym T        row pass      float pairs, two rows per lane
+//   C  4Z = W Q          column pass   float pairs, two columns per lane
+// with W = 2U, so 4Z is the same exact integer the other kernels form and
+// the reconstruction is 4Z * 2^-(2 + 2 log2 N).
+//
+// Pass A packs two pixels of a row in one 32-bit word, as they lie in memory,
+// and applies T to both columns with one integer add per butterfly add: the
+// word w = x1 * 2^16 + x0 is linear in the pair, and every output of T
+// satisfies |X| <= 255 N < 2^15, so both halves decode exactly at the end.
+// Int16 pixels are biased by 2^15 on load (bit 15 flipped); T maps the bias
+// to its DC row only (every other row of T sums to zero), where it is
+// subtracted.  Passes B and C hold two values of the same index of two rows
+// (B) or of two columns (C) in one f32x2 register pair, so that every add of
+// the butterflies is one packed instruction.  All values are integers (times
+// a power of two); the largest any stage of this order can form at r = N^2/4
+// is below 2^23 (tests/test_float_exact.py computes the exact worst case
+// over inputs in [-255, 255]), so every float operation is exact and the
+// reconstruction is bit-identical to the integer kernels'.
+//
+// Signs and factors of two of the butterflies are carried lazily (LV): a
+// value is s * v with s a small signed power of two known at compile time,
+// folded into the next packed add, subtract or multiply-add.  Values known
+// to be zero (pruned by the zonal extent) cost nothing.  The per-column
+// factors left on the outputs of pass B are the same for every lane; pass C
+// multiplies them into its output scale.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "block_kernels.cuh"
+#include "ptx.cuh"
+
+namespace cdct {
+
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 kpair(float c) { return pk2(c, c); }
+
+// Lazy packed value: s * v, or zero when z.  s and z are compile-time
+// constants once the butterflies are unrolled and inlined.
+struct LV {
+  f32x2 v;
+  bool z;
+  int s;
+};
+__device__ __forceinline__ LV lv(f32x2 v) { return LV{v, false, 1}; }
+__device__ __forceinline__ LV lv_zero() { return LV{0ull, true, 0}; }
+__device__ __forceinline__ LV operator-(LV a) {
+  a.s = -a.s;
+  return a;
+}
+__device__ __forceinline__ LV operator+(LV a, LV b) {
+  if (a.z) return b;
+  if (b.z) return a;
+  if (a.s == b.s) return LV{add2(a.v, b.v), false, a.s};
+  if (a.s == -b.s) return LV{sub2(a.v, b.v), false, a.s};
+  const int ma = a.s < 0 ? -a.s : a.s, mb = b.s < 0 ? -b.s : b.s;
+  if (ma <= mb) return LV{fma2(b.v, kpair(static_cast<float>(b.s / a.s)), a.v), false, a.s};
+  return LV{fma2(a.v, kpair(static_cast<float>(a.s / b.s)), b.v), false, b.s};
+}
+__device__ __forceinline__ LV operator-(LV a, LV b) { return a + (-b); }
+__device__ __forceinline__ LV operator*(int c, LV a) {
+  if (c == 0 || a.z) return lv_zero();
+  a.s *= c;
+  return a;
+}
+
+// 16-bit-biased halves of a word as floats 1.5 * 2^23 + half (exact)
+__device__ __forceinline__ float magic_lo16(uint32_t w) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, 0x7610;" : "=r"(r) : "r"(w), "r"(0x4B400000u));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ float magic_hi16(uint32_t w) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(r) : "r"(w), "r"(0x4B400000u));
+  return __uint_as_float(r);
+}
+// bytes 0 and 1 of a word as floats 1.5 * 2^23 + byte
+__device__ __forceinline__ float magic_b0(uint32_t w) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, 0x7640;" : "=r"(r) : "r"(w), "r"(0x4B400000u));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ float magic_b1(uint32_t w) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, 0x7641;" : "=r"(r) : "r"(w), "r"(0x4B400000u));
+  return __uint_as_float(r);
+}
+// two u8 pixels (bytes 0, 1 of w) as the word p0 + p1 * 2^16
+__device__ __forceinline__ uint32_t spread_u8x2(uint32_t w) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, 0, 0x4140;" : "=r"(r) : "r"(w));
+  return r;
+}
+
+__device__ __forceinline__ void stcs_f2(float* p, f32x2 v) {
+  float lo, hi;
+  unpk2(v, lo, hi);
+  __stcs(reinterpret_cast<float2*>(p), make_float2(lo, hi));
+}
+__device__ __forceinline__ void stcs_f4(float* p, f32x2 a, f32x2 b) {
+  float a0, a1, b0, b1;
+  unpk2(a, a0, a1);
+  unpk2(b, b0, b1);
+  __stcs(reinterpret_cast<float4*>(p), make_float4(a0, a1, b0, b1));
+}
+
+// Two pixels of a staged row (columns x and x + 1 of the block at sblk,
+// clamped to the block's `valid` columns) as one packed word of pass A.
+template <typename InT>
+__device__ __forceinline__ uint32_t stage_pair_word(const unsigned char* row, int x, int valid) {
+  const InT* p = reinterpret_cast<const InT*>(row);
+  if (x + 1 < valid) {
+    if constexpr (sizeof(InT) == 2)
+      return *reinterpret_cast<const uint32_t*>(p + x) ^ 0x8000u;
+    else
+      return spread_u8x2(*reinterpret_cast<const uint16_t*>(p + x));
+  }
+  const uint32_t a = static_cast<uint32_t>(p[min(x, valid - 1)]) & (sizeof(InT) == 2 ? 0xFFFFu : 0xFFu);
+  const uint32_t b = static_cast<uint32_t>(p[min(x + 1, valid - 1)]) & (sizeof(InT) == 2 ? 0xFFFFu : 0xFFu);
+  return sizeof(InT) == 2 ? ((a | (b << 16)) ^ 0x8000u) : (a | (b << 16));
+}
+
+// A pass-A input word (two pixels; int16 with the low half's bit 15 flipped,
+// u8 spread to 16-bit halves) back as a pair of exact floats.
+template <typename InT>
+__device__ __forceinline__ f32x2 input_word_ref(uint32_t w) {
+  if constexpr (sizeof(InT) == 2) {
+    const uint32_t b = w ^ 0x80000000u;                  // both halves biased by 2^15
+    return add2(pk2(magic_lo16(b), magic_hi16(b)), kpair(-kMagicI16));
+  } else {
+    return add2(pk2(magic_lo16(w), magic_hi16(w)), kpair(-kMagicU8));
+  }
+}
+
+// Words of pass A as exact floats (1.5 * 2^23 + X + 2^15 minus the magic).
+__device__ __forceinline__ f32x2 xa_pair_lo(uint32_t w_row0, uint32_t w_row1) {
+  return add2(pk2(magic_lo16(w_row0), magic_lo16(w_row1)), kpair(-kMagicI16));
+}
+__device__ __forceinline__ f32x2 xa_pair_hi(uint32_t w_row0, uint32_t w_row1) {
+  return add2(pk2(magic_hi16(w_row0), magic_hi16(w_row1)), kpair(-kMagicI16));
+}
+
+// Pass-A outputs X (rows 0 .. EA-1 of the lane's column pair) as biased
+// words: each half is X + 2^15, the form the pass-B reads decode.
+template <int N, class P, typename InT, int EA>
+__device__ __forceinline__ void pass_a(uint32_t (&w)[N], uint32_t (&xo)[EA]) {
+  Jam<N, P>::T(w);
+#pragma unroll
+  for (int i = 0; i < EA; ++i) xo[i] = w[i] + 0x80008000u;
+  if constexpr (sizeof(InT) == 2) xo[0] -= static_cast<uint32_t>(N) * 0x8000u;   // the input bias, on the DC row
+}
+
+// Pass B for one row pair: x holds the decoded X rows (2r, 2r+1) as pairs;
+// on return it holds Q = 2Ym T of those rows (raw values, factors s_j
+// pending), with `mt` the pair masks of the rows' zig-zag positions.  With
+// APPLY false the mask multiplies are left out (the factors are the same).
+template <int N, class P, int E, bool APPLY>
+__device__ __forceinline__ void pass_b(LV (&x)[N], const f32x2* mt) {
+  Jam<N, P>::Wt(x);                           // 2Y = X W  (each row times 2U)
+#pragma unroll
+  for (int j = 0; j < N; j += 2) {
+    if (j < E) {                              // zonal mask (0 or 1 per value), two columns per 128-bit read
+      if constexpr (APPLY) {
+        const uint4 m = *reinterpret_cast<const uint4*>(mt + j);
+        x[j].v = mul2(x[j].v, (static_cast<f32x2>(m.y) << 32) | m.x);
+        if (j + 1 < E) x[j + 1].v = mul2(x[j + 1].v, (static_cast<f32x2>(m.w) << 32) | m.z);
+      }
+      if (j + 1 >= E) x[j + 1] = lv_zero();
+    } else {
+      x[j] = lv_zero();
+      x[j + 1] = lv_zero();
+    }
+  }
+  Jam<N, P>::Tt(x);                           // Q = 2Ym T
+}
+
+// the factors s_j pass B leaves on its outputs: the same structure run on
+// placeholder values (the factors do not depend on the values)
+template <int N, class P, int E>
+__device__ __forceinline__ void pass_b_factors(float* out) {
+  LV x[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) x[j] = lv(0ull);
+  pass_b<N, P, E, false>(x, nullptr);
+#pragma unroll
+  for (int j = 0; j < N; ++j) out[j] = x[j].z ? 0.f : static_cast<float>(x[j].s);
+}
+
+// keep(i, j) of the zig-zag cut at r
+__device__ __forceinline__ float keep_f(int n, int r, int i, int j) { return zigzag_pos(n, i, j) < r ? 1.f : 0.f; }
+
+// ---------------------------------------------------------------------------
+// N = 32: a warp owns 2 blocks.  Pass A / C: lane = (block lane >> 4, column
+// pair c = lane & 15).  Pass B: lanes 0..23 = (block lane / 12, row pair
+// lane % 12); rows >= E (23 at r = 256) are never kept.
+// Exchange buffer per warp (words), aliased by the two exchanges:
+//   xA: block b, column pair c, row i at  b*472 + c*28 + i      (24 rows)
+//   xB: 16-byte chunk (Q[2r][2c], Q[2r][2c+1], Q[2r+1][2c], Q[2r+1][2c+1])
+//       at chunk  b*212 + c*13 + r
+// The pads make every 64/128-bit access of a quarter / half warp hit
+// distinct banks (tests/test_smem_banks.py).
+// ---------------------------------------------------------------------------
+template <class P, typename InT, int RFIX>
+struct SepBody32 {
+  static constexpr int N = 32;
+  static constexpr int E = zonal_extent(32, RFIX);
+  static constexpr int EA = (E + 3) & ~3;
+  static constexpr int RP = EA / 2;
+  static_assert(RP <= 16 && 2 * RP <= 32, "row pairs per block");
+  static constexpr int XA_C = 28, XA_B = 472;
+  static constexpr int XB_C = 13, XB_B = 212;
+  static_assert(EA <= XA_C && RP <= XB_C, "exchange pads");
+  static constexpr int XCH_WARP_WORDS = (4 * (XB_B + 16 * XB_C) > 2 * XA_B) ? 4 * (XB_B + 16 * XB_C) : 2 * XA_B;
+  static constexpr int MT_STRIDE = 26;                  // pairs per row pair in the mask table (even, bank spread)
+  static_assert(MT_STRIDE >= E + (E & 1), "mask table row");
+  // constant area (words): mask table [RP][MT_STRIDE] pairs, then factors s_j [32]
+  static constexpr int CONST_WORDS = RP * MT_STRIDE * 2 + 32;
+  static constexpr int TASKS_B = 2 * RP;
+
+  struct Ctx {
+    int mt;              // pass B: the lane's row-pair masks (pair offset in the mask table)
+    int xb_r;            // pass B: block * XB_B + r (chunks); lane >= TASKS_B: no stores
+    int xa_r;            // pass B: block * XA_B + 2r (words)
+    bool b_active;
+    f32x2 scl;           // pass C: s_{2c}, s_{2c+1} times the output scale
+  };
+
+  // fills the constant area (all threads of the CTA, before the CTA barrier)
+  static __device__ __forceinline__ void init_const(float* cbuf, int tid) {
+    for (int k = tid; k < RP * E; k += kThreads) {
+      const int r = k / E, j = k - r * E;
+      cbuf[2 * (r * MT_STRIDE + j)] = keep_f(32, RFIX, 2 * r, j);
+      cbuf[2 * (r * MT_STRIDE + j) + 1] = keep_f(32, RFIX, 2 * r + 1, j);
+    }
+    if (tid == 0) pass_b_factors<32, P, E>(cbuf + RP * MT_STRIDE * 2);
+  }
+  static __device__ __forceinline__ void init(Ctx& c, const BlockArgs& a, int lane, const float* cbuf) {
+    c.b_active = lane < TASKS_B;
+    const int t = c.b_active ? lane : TASKS_B - 1;
+    const int bb = t / RP, r = t - bb * RP;
+    c.mt = r * MT_STRIDE;
+    c.xb_r = bb * XB_B + r;
+    c.xa_r = bb * XA_B + 2 * r;
+    const float* sf = cbuf + RP * MT_STRIDE * 2;
+    const int col = 2 * (lane & 15);
+    c.scl = pk2(sf[col] * a.scale, sf[col + 1] * a.scale);
+  }
+
+  static constexpr bool EARLY_RELEASE = true;
+  template <class Rel>
+  static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, int* xch, const float* cbuf,
+                                              int lane, const Ctx& cx, Rel&& release) {
+    const int blk = lane >> 4, c = lane & 15;
+    uint32_t* xw = reinterpret_cast<uint32_t*>(xch);
+    // ---- pass A: X = T A on the column pair (2c, 2c+1) --------------------
+    uint32_t ref[32];
+    {
+      uint32_t w[32];
+      const unsigned char* col = up.sblk + 2 * c * static_cast<int>(sizeof(InT));
+      if (up.valid == 32) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const unsigned char* row = col + i * up.spitch;
+          if constexpr (sizeof(InT) == 2) w[i] = *reinterpret_cast<const uint32_t*>(row) ^ 0x8000u;
+          else w[i] = spread_u8x2(*reinterpret_cast<const uint16_t*>(row));
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) w[i] = stage_pair_word<InT>(up.sblk + i * up.spitch, 2 * c, up.valid);
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) ref[i] = w[i];   // the pixels the squared error compares with
+      uint32_t xo[EA];
+      pass_a<32, P, InT, EA>(w, xo);
+      uint32_t* dst = xw + blk * XA_B + c * XA_C;
+#pragma unroll
+      for (int q = 0; q < EA / 4; ++q)
+        *reinterpret_cast<uint4*>(dst + 4 * q) = make_uint4(xo[4 * q], xo[4 * q + 1], xo[4 * q + 2], xo[4 * q + 3]);
+    }
+    release();                                 // the stage is not read again: its refill overlaps passes B and C
+    // ---- pass B: rows (2r, 2r+1) -------------------------------------------
+    LV x[32];
+    {
+      const uint32_t* src = xw + cx.xa_r;
+#pragma unroll
+      for (int cp = 0; cp < 16; ++cp) {
+        const uint2 ww = *reinterpret_cast<const uint2*>(src + cp * XA_C);
+        x[2 * cp] = lv(xa_pair_lo(ww.x, ww.y));
+        x[2 * cp + 1] = lv(xa_pair_hi(ww.x, ww.y));
+      }
+    }
+    __syncwarp();                              // every pass-A word is read before pass B overwrites the buffer
+    pass_b<32, P, E, true>(x, reinterpret_cast<const f32x2*>(cbuf) + cx.mt);
+    if (cx.b_active) {
+      f32x2* dst = reinterpret_cast<f32x2*>(xch) + 2 * cx.xb_r;
+#pragma unroll
+      for (int cp = 0; cp < 16; ++cp) {
+        float a0, a1, b0, b1;
+        unpk2(x[2 * cp].z ? 0ull : x[2 * cp].v, a0, a1);
+        unpk2(x[2 * cp + 1].z ? 0ull : x[2 * cp + 1].v, b0, b1);
+        *reinterpret_cast<float4*>(dst + 2 * cp * XB_C) = make_float4(a0, b0, a1, b1);
+      }
+    }
+    __syncwarp();
+    // ---- pass C: 4Z = W Q on the column pair -------------------------------
+    LV q[32];
+    {
+      const float4* src = reinterpret_cast<const float4*>(xch) + blk * XB_B + c * XB_C;
+#pragma unroll
+      for (int rp = 0; rp < RP; ++rp) {
+        const float4 t = src[rp];
+        q[2 * rp] = lv(pk2(t.x, t.y));
+        q[2 * rp + 1] = lv(pk2(t.z, t.w));
+      }
+#pragma unroll
+      for (int i = E; i < 32; ++i) q[i] = lv_zero();
+    }
+    __syncwarp();                              // the buffer is free for the next unit's pass A
+    Jam<32, P>::W(q);
+    // ---- scale, store, squared error ----------------------------------------
+    f32x2 acc = 0ull;
+    if (!up.active) return 0.f;
+    const int x0 = 2 * c;
+    const bool err = a.partial != nullptr;
+    if (up.fast) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const f32x2 rec = q[i].z ? 0ull : mul2(q[i].v, mul2(cx.scl, kpair(static_cast<float>(q[i].s))));
+        stcs_f2(up.orow0 + i * up.out_pitch + x0, rec);
+        if (err) {
+          const f32x2 e = sub2(rec, input_word_ref<InT>(ref[i]));
+          acc = fma2(e, e, acc);
+        }
+      }
+    } else {
+      const bool v0 = x0 < up.valid, v1 = x0 + 1 < up.valid;
+      const f32x2 keep = pk2(v0 ? 1.f : 0.f, v1 ? 1.f : 0.f);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (up.by * 32 + i >= up.height) break;
+        const f32x2 rec = q[i].z ? 0ull : mul2(q[i].v, mul2(cx.scl, kpair(static_cast<float>(q[i].s))));
+        float r0, r1;
+        unpk2(rec, r0, r1);
+        float* orow = up.orow0 + i * up.out_pitch + x0;
+        if (v0) orow[0] = r0;
+        if (v1) orow[1] = r1;
+        if (err) {
+          const f32x2 e = mul2(sub2(rec, input_word_ref<InT>(ref[i])), keep);
+          acc = fma2(e, e, acc);
+        }
+      }
+    }
+    float lo, hi;
+    unpk2(acc, lo, hi);
+    return lo + hi;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// N = 16: a warp owns 8 blocks.  Pass A / C: lane = (block lane & 7, column
+// quad q = lane >> 3: columns 4q .. 4q+3, column pairs 2q, 2q+1).  Pass B:
+// 8 blocks x RP row pairs, in rounds of 32 lanes (task t: block t & 7, row
+// pair t >> 3).
+// Exchange buffer per warp (words), two disjoint regions (so that the rounds
+// of pass B can read and write in turn):
+//   xA: block b, column pair cp, row i at  b*100 + cp*12 + i      (12 rows)
+//   xB: 16-byte chunk (Q[2r][2cp], Q[2r][2cp+1], Q[2r+1][2cp], Q[2r+1][2cp+1])
+//       at chunk  200 + b*49 + cp*6 + r  (xB starts after xA's 800 words)
+// ---------------------------------------------------------------------------
+template <class P, typename InT, int RFIX>
+struct SepBody16 {
+  static constexpr int N = 16;
+  static constexpr int E = zonal_extent(16, RFIX);
+  static constexpr int EA = (E + 3) & ~3;
+  static constexpr int RP = EA / 2;
+  static constexpr int XA_C = 12, XA_B = 100;
+  static constexpr int XB_C = 6, XB_B = 49;
+  static_assert(EA <= XA_C && RP <= XB_C && 8 * XA_C <= XA_B && 8 * XB_C <= XB_B, "exchange pads");
+  static constexpr int XB_OFF = 8 * XA_B / 4;             // chunk where xB starts
+  static constexpr int XCH_WARP_WORDS = 8 * XA_B + 4 * 8 * XB_B;
+  static constexpr int MT_STRIDE = 12;
+  static_assert(MT_STRIDE >= E + (E & 1), "mask table row");
+  static constexpr int CONST_WORDS = RP * MT_STRIDE * 2 + 16;
+  static constexpr int TASKS_B = 8 * RP;
+  static constexpr int ROUNDS_B = (TASKS_B + 31) / 32;
+
+  struct Ctx {
+    f32x2 scl0, scl1;    // pass C: factors of columns (4q, 4q+1), (4q+2, 4q+3) times the output scale
+  };
+
+  static __device__ __forceinline__ void init_const(float* cbuf, int tid) {
+    for (int k = tid; k < RP * E; k += kThreads) {
+      const int r = k / E, j = k - r * E;
+      cbuf[2 * (r * MT_STRIDE + j)] = keep_f(16, RFIX, 2 * r, j);
+      cbuf[2 * (r * MT_STRIDE + j) + 1] = keep_f(16, RFIX, 2 * r + 1, j);
+    }
+    if (tid == 0) pass_b_factors<16, P, E>(cbuf + RP * MT_STRIDE * 2);
+  }
+  static __device__ __forceinline__ void init(Ctx& c, const BlockArgs& a, int lane, const float* cbuf) {
+    const float* sf = cbuf + RP * MT_STRIDE * 2;
+    const int col = 4 * (lane >> 3);
+    c.scl0 = pk2(sf[col] * a.scale, sf[col + 1] * a.scale);
+    c.scl1 = pk2(sf[col + 2] * a.scale, sf[col + 3] * a.scale);
+  }
+
+  static constexpr bool EARLY_RELEASE = true;
+  template <class Rel>
+  static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, int* xch, const float* cbuf,
+                                              int lane, const Ctx& cx, Rel&& release) {
+    const int blk = lane & 7, qd = lane >> 3;
+    uint32_t* xw = reinterpret_cast<uint32_t*>(xch);
+    // ---- pass A: X = T A on the column pairs (4q, 4q+1), (4q+2, 4q+3) ------
+    uint32_t ref0[16], ref1[16];
+    {
+      uint32_t w0[16], w1[16];
+      const int es = static_cast<int>(sizeof(InT));
+      if (up.valid == 16) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const unsigned char* row = up.sblk + i * up.spitch + 4 * qd * es;
+          if constexpr (sizeof(InT) == 2) {
+            const uint2 t = *reinterpret_cast<const uint2*>(row);
+            w0[i] = t.x ^ 0x8000u;
+            w1[i] = t.y ^ 0x8000u;
+          } else {
+            const uint32_t t = *reinterpret_cast<const uint32_t*>(row);
+            w0[i] = spread_u8x2(t);
+            w1[i] = spread_u8x2(t >> 16);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          w0[i] = stage_pair_word<InT>(up.sblk + i * up.spitch, 4 * qd, up.valid);
+          w1[i] = stage_pair_word<InT>(up.sblk + i * up.spitch, 4 * qd + 2, up.valid);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {           // the pixels the squared error compares with
+        ref0[i] = w0[i];
+        ref1[i] = w1[i];
+      }
+      uint32_t xo0[EA], xo1[EA];
+      pass_a<16, P, InT, EA>(w0, xo0);
+      pass_a<16, P, InT, EA>(w1, xo1);
+      uint32_t* d0 = xw + blk * XA_B + (2 * qd) * XA_C;
+      uint32_t* d1 = d0 + XA_C;
+#pragma unroll
+      for (int t = 0; t < EA / 4; ++t) {
+        *reinterpret_cast<uint4*>(d0 + 4 * t) = make_uint4(xo0[4 * t], xo0[4 * t + 1], xo0[4 * t + 2], xo0[4 * t + 3]);
+        *reinterpret_cast<uint4*>(d1 + 4 * t) = make_uint4(xo1[4 * t], xo1[4 * t + 1], xo1[4 * t + 2], xo1[4 * t + 3]);
+      }
+    }
+    release();                                 // the stage is not read again: its refill overlaps passes B and C
+    // ---- pass B: rounds of row-pair tasks -----------------------------------
+#pragma unroll 1
+    for (int rd = 0; rd < ROUNDS_B; ++rd) {
+      const int t = rd * 32 + lane;
+      const int tc = min(t, TASKS_B - 1);
+      const int bb = tc & 7, r = tc >> 3;
+      LV x[16];
+      const uint32_t* src = xw + bb * XA_B + 2 * r;
+#pragma unroll
+      for (int cp = 0; cp < 8; ++cp) {
+        const uint2 ww = *reinterpret_cast<const uint2*>(src + cp * XA_C);
+        x[2 * cp] = lv(xa_pair_lo(ww.x, ww.y));
+        x[2 * cp + 1] = lv(xa_pair_hi(ww.x, ww.y));
+      }
+      pass_b<16, P, E, true>(x, reinterpret_cast<const f32x2*>(cbuf) + r * MT_STRIDE);
+      if (t < TASKS_B) {
+        f32x2* dst = reinterpret_cast<f32x2*>(xch) + 2 * (XB_OFF + bb * XB_B + r);
+#pragma unroll
+        for (int cp = 0; cp < 8; ++cp) {
+          float a0, a1, b0, b1;
+          unpk2(x[2 * cp].z ? 0ull : x[2 * cp].v, a0, a1);
+          unpk2(x[2 * cp + 1].z ? 0ull : x[2 * cp + 1].v, b0, b1);
+          *reinterpret_cast<float4*>(dst + 2 * cp * XB_C) = make_float4(a0, b0, a1, b1);
+        }
+      }
+    }
+    __syncwarp();
+    // ---- pass C: 4Z = W Q on the two column pairs ---------------------------
+    LV q0[16], q1[16];
+    {
+      const float4* s0 = reinterpret_cast<const float4*>(xch) + XB_OFF + blk * XB_B + (2 * qd) * XB_C;
+      const float4* s1 = s0 + XB_C;
+#pragma unroll
+      for (int rp = 0; rp < RP; ++rp) {
+        const float4 t0 = s0[rp], t1 = s1[rp];
+        q0[2 * rp] = lv(pk2(t0.x, t0.y));
+        q0[2 * rp + 1] = lv(pk2(t0.z, t0.w));
+        q1[2 * rp] = lv(pk2(t1.x, t1.y));
+        q1[2 * rp + 1] = lv(pk2(t1.z, t1.w));
+      }
+#pragma unroll
+      for (int i = E; i < 16; ++i) {
+        q0[i] = lv_zero();
+        q1[i] = lv_zero();
+      }
+    }
+    __syncwarp();
+    Jam<16, P>::W(q0);
+    Jam<16, P>::W(q1);
+    // ---- scale, store, squared error ----------------------------------------
+    f32x2 acc = 0ull;
+    if (!up.active) return 0.f;
+    const int x0 = 4 * qd;
+    const bool err = a.partial != nullptr;
+    if (up.fast) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const f32x2 r0 = q0[i].z ? 0ull : mul2(q0[i].v, mul2(cx.scl0, kpair(static_cast<float>(q0[i].s))));
+        const f32x2 r1 = q1[i].z ? 0ull : mul2(q1[i].v, mul2(cx.scl1, kpair(static_cast<float>(q1[i].s))));
+        stcs_f4(up.orow0 + i * up.out_pitch + x0, r0, r1);
+        if (err) {
+          const f32x2 e0 = sub2(r0, input_word_ref<InT>(ref0[i])), e1 = sub2(r1, input_word_ref<InT>(ref1[i]));
+          acc = fma2(e0, e0, acc);
+          acc = fma2(e1, e1, acc);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (up.by * 16 + i >= up.height) break;
+        const f32x2 rr[2] = {q0[i].z ? 0ull : mul2(q0[i].v, mul2(cx.scl0, kpair(static_cast<float>(q0[i].s)))),
+                             q1[i].z ? 0ull : mul2(q1[i].v, mul2(cx.scl1, kpair(static_cast<float>(q1[i].s))))};
+        float* orow = up.orow0 + i * up.out_pitch + x0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v0, v1;
+          unpk2(rr[h], v0, v1);
+          const int c0 = x0 + 2 * h;
+          if (c0 < up.valid) orow[2 * h] = v0;
+          if (c0 + 1 < up.valid) orow[2 * h + 1] = v1;
+          if (err) {
+            const f32x2 e = mul2(sub2(rr[h], input_word_ref<InT>(h == 0 ? ref0[i] : ref1[i])),
+                                 pk2(c0 < up.valid ? 1.f : 0.f, c0 + 1 < up.valid ? 1.f : 0.f));
+            acc = fma2(e, e, acc);
+          }
+        }
+      }
+    }
+    float lo, hi;
+    unpk2(acc, lo, hi);
+    return lo + hi;
+  }
+};
+
+}  // namespace cdct
