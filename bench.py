@@ -569,7 +569,7 @@ def e2e_frames(args, dev, luma_p, chroma_p, schedule, px_step, world, max_over_r
     out_free = [torch.cuda.Event() for _ in range(2)]     # reconstructions of set k copied out
     pass_done = {}
 
-    def step(i):
+    def step(i, compute=True):
         k = i % 2
         fs = sets[k]
         with torch.cuda.stream(up):
@@ -585,7 +585,11 @@ def e2e_frames(args, dev, luma_p, chroma_p, schedule, px_step, world, max_over_r
                 ev = torch.cuda.Event()
                 ev.record(comp)
                 pass_done[p] = ev
-            fs.run(comp, after_pass=after)
+            if compute:
+                fs.run(comp, after_pass=after)
+            else:
+                for p in passes:
+                    after(p)
             in_free[k].record(comp)
         with torch.cuda.stream(down):
             o = 0
@@ -618,6 +622,19 @@ def e2e_frames(args, dev, luma_p, chroma_p, schedule, px_step, world, max_over_r
     barrier()
     e2e_ms = max_over_ranks(e_start.elapsed_time(e_end))
     ps = psnr_host.numpy()
+    # the same copies with the passes left out: what the two links sustain together
+    c_start, c_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c_start.record(comp)
+    up.wait_event(c_start)
+    down.wait_event(c_start)
+    for i in range(e2e_steps):
+        step(i, compute=False)
+    comp.wait_stream(up)
+    comp.wait_stream(down)
+    c_end.record(comp)
+    torch.cuda.synchronize()
+    copies_ms = c_start.elapsed_time(c_end) / e2e_steps
     assert np.all(np.isfinite(ps)) and ps.min() > 0, "PSNR check failed"
     last = sets[(e2e_steps - 1) % 2]
     assert torch.equal(host_y[passes[-1]][-1], last.recon_y_of[passes[-1]][-1].cpu()), "read-back check failed"
@@ -630,6 +647,7 @@ def e2e_frames(args, dev, luma_p, chroma_p, schedule, px_step, world, max_over_r
                          "measured": "plain pinned copies of one step's inputs (h2d) and one pass's "
                                      "reconstructions (d2h), 5 each, CUDA events"},
             "copy_bound_ms_per_step": round(max(h2d / h2d_gbs, d2h / d2h_gbs) / 1e6, 3),
+            "copies_only_ms_per_step": round(copies_ms, 3),
             "readback": "every pass's float32 reconstructions (luma + chroma) and PSNRs, to pinned host memory",
             "pipelining": "3 streams: host-to-device a step ahead (2 device input sets), each pass's "
                           "reconstructions copied back as it ends (2 device output sets), passes on a compute stream"}

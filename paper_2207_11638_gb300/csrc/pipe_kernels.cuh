@@ -672,6 +672,11 @@ struct FoldBody {
     c.mask = a.slab_mask[B::sub_block(lane)];
   }
   static constexpr bool EARLY_RELEASE = false;
+  // block of the unit a thread works on: N = 8 one per thread; N = 16 eight
+  // per warp (lane & 7); N = 32 two per warp (lane >> 4)
+  static __device__ __forceinline__ int lane_block(int warp, int lane) {
+    return N == 8 ? warp * 32 + lane : (N == 16 ? warp * 8 + (lane & 7) : warp * 2 + (lane >> 4));
+  }
   template <class Rel>
   static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, int* xch, const float*, int lane,
                                               const Ctx& cx, Rel&& release) {
@@ -784,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES, BODY>::value) fzi
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int* xch = xch_all + warp * Body::XCH_WARP_WORDS;
   // block of this thread within the unit
-  const int lb = (N == 8) ? tid : (N == 16 ? warp * 8 + (lane & 7) : warp * 2 + (lane >> 4));
+  const int lb = Body::lane_block(warp, lane);
   // input lines are read once (evict first), or a second time from L2 by a
   // body that releases its stage early and reads the pixels it compares with
   // from global memory (normal priority)
@@ -888,7 +893,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES, BODY>::value) fzi
       up.spitch = d.width * es;
       up.sblk = up.active ? stage + k * N * up.spitch + up.bx * N * es : stage;
       const int wb = N == 16 ? 8 : (N == 32 ? 2 : 1);       // blocks per warp
-      const int lb0 = lb - (N == 16 ? (lane & 7) : (N == 32 ? (lane >> 4) : 0));
+      const int lb0 = warp * wb;                              // the warp's first block
       up.wrow = (lb0 % d.nbx) + wb <= d.nbx;
     }
     up.valid = up.active ? min(N, d.width - up.bx * N) : N;

@@ -45,15 +45,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, ui
 // Wait for phase `parity` of the barrier, giving up after about `limit`
 // SM cycles (the bulk copies it tracks then failed to land).  Returns false
 // on time-out; the caller records the error and stops.
-// Between polls the warp sleeps (exponential backoff up to 256 ns) so that a
-// waiting warp does not take issue slots from the warps that compute.
+// Each try_wait suspends the warp in hardware until the phase completes or
+// the hardware's own time limit passes, so the poll loop takes few issue
+// slots and the warp resumes as soon as its data has landed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  unsigned ns = 16;
   while (!mbar_try_wait(bar, parity)) {
-    __nanosleep(ns);
-    if (ns < 256) ns <<= 1;
     if (clock64() - t0 > limit) return false;
   }
   return true;

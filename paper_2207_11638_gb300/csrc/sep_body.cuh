@@ -228,8 +228,12 @@ struct SepBody32 {
   static constexpr int XCH_WARP_WORDS = (4 * (XB_B + 16 * XB_C) > 2 * XA_B) ? 4 * (XB_B + 16 * XB_C) : 2 * XA_B;
   static constexpr int MT_STRIDE = 26;                  // pairs per row pair in the mask table (even, bank spread)
   static_assert(MT_STRIDE >= E + (E & 1), "mask table row");
-  // constant area (words): mask table [RP][MT_STRIDE] pairs, then factors s_j [32]
-  static constexpr int CONST_WORDS = RP * MT_STRIDE * 2 + 32;
+  // constant area (words): the mask table [RP][MT_STRIDE] pairs twice (the
+  // lanes of the warp's second block read the second copy, 156 chunks on, so
+  // that rows r and r + 8 read in one quarter warp fall in different banks),
+  // then the factors s_j [32]
+  static constexpr int MT_WORDS = RP * MT_STRIDE * 2;
+  static constexpr int CONST_WORDS = 2 * MT_WORDS + 32;
   static constexpr int TASKS_B = 2 * RP;
 
   struct Ctx {
@@ -244,24 +248,28 @@ struct SepBody32 {
   static __device__ __forceinline__ void init_const(float* cbuf, int tid) {
     for (int k = tid; k < RP * E; k += kThreads) {
       const int r = k / E, j = k - r * E;
-      cbuf[2 * (r * MT_STRIDE + j)] = keep_f(32, RFIX, 2 * r, j);
-      cbuf[2 * (r * MT_STRIDE + j) + 1] = keep_f(32, RFIX, 2 * r + 1, j);
+      const float k0 = keep_f(32, RFIX, 2 * r, j), k1 = keep_f(32, RFIX, 2 * r + 1, j);
+      cbuf[2 * (r * MT_STRIDE + j)] = k0;
+      cbuf[2 * (r * MT_STRIDE + j) + 1] = k1;
+      cbuf[MT_WORDS + 2 * (r * MT_STRIDE + j)] = k0;
+      cbuf[MT_WORDS + 2 * (r * MT_STRIDE + j) + 1] = k1;
     }
-    if (tid == 0) pass_b_factors<32, P, E>(cbuf + RP * MT_STRIDE * 2);
+    if (tid == 0) pass_b_factors<32, P, E>(cbuf + 2 * MT_WORDS);
   }
   static __device__ __forceinline__ void init(Ctx& c, const BlockArgs& a, int lane, const float* cbuf) {
     c.b_active = lane < TASKS_B;
     const int t = c.b_active ? lane : TASKS_B - 1;
     const int bb = t / RP, r = t - bb * RP;
-    c.mt = r * MT_STRIDE;
+    c.mt = bb * (MT_WORDS / 2) + r * MT_STRIDE;
     c.xb_r = bb * XB_B + r;
     c.xa_r = bb * XA_B + 2 * r;
-    const float* sf = cbuf + RP * MT_STRIDE * 2;
+    const float* sf = cbuf + 2 * MT_WORDS;
     const int col = 2 * (lane & 15);
     c.scl = pk2(sf[col] * a.scale, sf[col + 1] * a.scale);
   }
 
   static constexpr bool EARLY_RELEASE = true;
+  static __device__ __forceinline__ int lane_block(int warp, int lane) { return warp * 2 + (lane >> 4); }
   template <class Rel>
   static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, int* xch, const float* cbuf,
                                               int lane, const Ctx& cx, Rel&& release) {
@@ -337,15 +345,19 @@ struct SepBody32 {
     if (!up.active) return 0.f;
     const int x0 = 2 * c;
     const bool err = a.partial != nullptr;
-    if (up.fast) {
+    if (up.fast && err) {
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const f32x2 rec = q[i].z ? 0ull : mul2(q[i].v, mul2(cx.scl, kpair(static_cast<float>(q[i].s))));
         stcs_f2(up.orow0 + i * up.out_pitch + x0, rec);
-        if (err) {
-          const f32x2 e = sub2(rec, input_word_ref<InT>(ref[i]));
-          acc = fma2(e, e, acc);
-        }
+        const f32x2 e = sub2(rec, input_word_ref<InT>(ref[i]));
+        acc = fma2(e, e, acc);
+      }
+    } else if (up.fast) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const f32x2 rec = q[i].z ? 0ull : mul2(q[i].v, mul2(cx.scl, kpair(static_cast<float>(q[i].s))));
+        stcs_f2(up.orow0 + i * up.out_pitch + x0, rec);
       }
     } else {
       const bool v0 = x0 < up.valid, v1 = x0 + 1 < up.valid;
@@ -372,15 +384,16 @@ struct SepBody32 {
 };
 
 // ---------------------------------------------------------------------------
-// N = 16: a warp owns 8 blocks.  Pass A / C: lane = (block lane & 7, column
-// quad q = lane >> 3: columns 4q .. 4q+3, column pairs 2q, 2q+1).  Pass B:
-// 8 blocks x RP row pairs, in rounds of 32 lanes (task t: block t & 7, row
-// pair t >> 3).
+// N = 16: a warp owns 8 blocks.  Pass A / C: lane l = (block b, column quad
+// q: columns 4q .. 4q+3, column pairs 2q, 2q+1) with b = (l & 3) + 4 (l >> 4),
+// q = (l >> 2) & 3, so that each half warp reads 128 contiguous bytes of a
+// staged row.  Pass B: 8 blocks x RP row pairs, in rounds of 32 lanes (task
+// t: block t & 7, row pair t >> 3).
 // Exchange buffer per warp (words), two disjoint regions (so that the rounds
 // of pass B can read and write in turn):
-//   xA: block b, column pair cp, row i at  b*100 + cp*12 + i      (12 rows)
+//   xA: column pair cp, block b, row i at  cp*104 + b*12 + i     (12 rows)
 //   xB: 16-byte chunk (Q[2r][2cp], Q[2r][2cp+1], Q[2r+1][2cp], Q[2r+1][2cp+1])
-//       at chunk  200 + b*49 + cp*6 + r  (xB starts after xA's 800 words)
+//       at chunk  208 + b*49 + cp*6 + r  (xB starts after xA's 832 words)
 // ---------------------------------------------------------------------------
 template <class P, typename InT, int RFIX>
 struct SepBody16 {
@@ -388,11 +401,11 @@ struct SepBody16 {
   static constexpr int E = zonal_extent(16, RFIX);
   static constexpr int EA = (E + 3) & ~3;
   static constexpr int RP = EA / 2;
-  static constexpr int XA_C = 12, XA_B = 100;
+  static constexpr int XA_R = 12, XA_CP = 104;            // words per block, per column pair
   static constexpr int XB_C = 6, XB_B = 49;
-  static_assert(EA <= XA_C && RP <= XB_C && 8 * XA_C <= XA_B && 8 * XB_C <= XB_B, "exchange pads");
-  static constexpr int XB_OFF = 8 * XA_B / 4;             // chunk where xB starts
-  static constexpr int XCH_WARP_WORDS = 8 * XA_B + 4 * 8 * XB_B;
+  static_assert(EA <= XA_R && RP <= XB_C && 8 * XA_R <= XA_CP && 8 * XB_C <= XB_B, "exchange pads");
+  static constexpr int XB_OFF = 8 * XA_CP / 4;            // chunk where xB starts
+  static constexpr int XCH_WARP_WORDS = 8 * XA_CP + 4 * 8 * XB_B;
   static constexpr int MT_STRIDE = 12;
   static_assert(MT_STRIDE >= E + (E & 1), "mask table row");
   static constexpr int CONST_WORDS = RP * MT_STRIDE * 2 + 16;
@@ -411,9 +424,12 @@ struct SepBody16 {
     }
     if (tid == 0) pass_b_factors<16, P, E>(cbuf + RP * MT_STRIDE * 2);
   }
+  static __device__ __forceinline__ int lane_blk(int lane) { return (lane & 3) + 4 * (lane >> 4); }
+  static __device__ __forceinline__ int lane_quad(int lane) { return (lane >> 2) & 3; }
+  static __device__ __forceinline__ int lane_block(int warp, int lane) { return warp * 8 + lane_blk(lane); }
   static __device__ __forceinline__ void init(Ctx& c, const BlockArgs& a, int lane, const float* cbuf) {
     const float* sf = cbuf + RP * MT_STRIDE * 2;
-    const int col = 4 * (lane >> 3);
+    const int col = 4 * lane_quad(lane);
     c.scl0 = pk2(sf[col] * a.scale, sf[col + 1] * a.scale);
     c.scl1 = pk2(sf[col + 2] * a.scale, sf[col + 3] * a.scale);
   }
@@ -422,7 +438,7 @@ struct SepBody16 {
   template <class Rel>
   static __device__ __forceinline__ float run(const BlockArgs& a, const UnitPos& up, int* xch, const float* cbuf,
                                               int lane, const Ctx& cx, Rel&& release) {
-    const int blk = lane & 7, qd = lane >> 3;
+    const int blk = lane_blk(lane), qd = lane_quad(lane);
     uint32_t* xw = reinterpret_cast<uint32_t*>(xch);
     // ---- pass A: X = T A on the column pairs (4q, 4q+1), (4q+2, 4q+3) ------
     uint32_t ref0[16], ref1[16];
@@ -458,8 +474,8 @@ struct SepBody16 {
       uint32_t xo0[EA], xo1[EA];
       pass_a<16, P, InT, EA>(w0, xo0);
       pass_a<16, P, InT, EA>(w1, xo1);
-      uint32_t* d0 = xw + blk * XA_B + (2 * qd) * XA_C;
-      uint32_t* d1 = d0 + XA_C;
+      uint32_t* d0 = xw + (2 * qd) * XA_CP + blk * XA_R;
+      uint32_t* d1 = d0 + XA_CP;
 #pragma unroll
       for (int t = 0; t < EA / 4; ++t) {
         *reinterpret_cast<uint4*>(d0 + 4 * t) = make_uint4(xo0[4 * t], xo0[4 * t + 1], xo0[4 * t + 2], xo0[4 * t + 3]);
@@ -474,10 +490,10 @@ struct SepBody16 {
       const int tc = min(t, TASKS_B - 1);
       const int bb = tc & 7, r = tc >> 3;
       LV x[16];
-      const uint32_t* src = xw + bb * XA_B + 2 * r;
+      const uint32_t* src = xw + bb * XA_R + 2 * r;
 #pragma unroll
       for (int cp = 0; cp < 8; ++cp) {
-        const uint2 ww = *reinterpret_cast<const uint2*>(src + cp * XA_C);
+        const uint2 ww = *reinterpret_cast<const uint2*>(src + cp * XA_CP);
         x[2 * cp] = lv(xa_pair_lo(ww.x, ww.y));
         x[2 * cp + 1] = lv(xa_pair_hi(ww.x, ww.y));
       }
@@ -521,17 +537,22 @@ struct SepBody16 {
     if (!up.active) return 0.f;
     const int x0 = 4 * qd;
     const bool err = a.partial != nullptr;
-    if (up.fast) {
+    if (up.fast && err) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const f32x2 r0 = q0[i].z ? 0ull : mul2(q0[i].v, mul2(cx.scl0, kpair(static_cast<float>(q0[i].s))));
         const f32x2 r1 = q1[i].z ? 0ull : mul2(q1[i].v, mul2(cx.scl1, kpair(static_cast<float>(q1[i].s))));
         stcs_f4(up.orow0 + i * up.out_pitch + x0, r0, r1);
-        if (err) {
-          const f32x2 e0 = sub2(r0, input_word_ref<InT>(ref0[i])), e1 = sub2(r1, input_word_ref<InT>(ref1[i]));
-          acc = fma2(e0, e0, acc);
-          acc = fma2(e1, e1, acc);
-        }
+        const f32x2 e0 = sub2(r0, input_word_ref<InT>(ref0[i])), e1 = sub2(r1, input_word_ref<InT>(ref1[i]));
+        acc = fma2(e0, e0, acc);
+        acc = fma2(e1, e1, acc);
+      }
+    } else if (up.fast) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const f32x2 r0 = q0[i].z ? 0ull : mul2(q0[i].v, mul2(cx.scl0, kpair(static_cast<float>(q0[i].s))));
+        const f32x2 r1 = q1[i].z ? 0ull : mul2(q1[i].v, mul2(cx.scl1, kpair(static_cast<float>(q1[i].s))));
+        stcs_f4(up.orow0 + i * up.out_pitch + x0, r0, r1);
       }
     } else {
 #pragma unroll

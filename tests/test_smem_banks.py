@@ -107,3 +107,82 @@ def test_staged_row_reads(esize):
     # N = 16: lanes of a quarter warp read one row of 8 consecutive blocks
     ad = [(l >> 3) * 4 * 512 * esize + (l & 7) * 16 * esize for l in range(32)]
     assert wavefronts(ad) == (8 if esize == 2 else 4)
+
+
+# ---- separable packed bodies (csrc/sep_body.cuh), paper convention, r = N^2/4
+# N = 32: lane -> (block lane >> 4, column pair lane & 15); pass-B task
+# t = min(lane, 23) -> (block t // 12, row pair t % 12).  Exchange words:
+# xA b*472 + c*28 + i; xB chunk b*212 + c*13 + r; mask table pairs
+# b*312 + r*26 + j (two copies).
+def sep32_task(l):
+    t = min(l, 23)
+    return t // 12, t % 12
+
+
+def test_sep32_accesses_conflict_free():
+    for i in range(32):      # pass A: staged row i (528-byte pitch), 4 bytes per lane
+        assert wavefronts([(l >> 4) * 64 + 4 * (l & 15) + i * 528 for l in range(32)], 4) == 1
+    for q in range(6):       # xA writes, 4 rows per 128-bit store
+        assert wavefronts([4 * ((l >> 4) * 472 + (l & 15) * 28 + 4 * q) for l in range(32)]) == 4
+    for cp in range(16):     # pass B reads of xA (rows 2r, 2r + 1)
+        ad = [4 * (sep32_task(l)[0] * 472 + 2 * sep32_task(l)[1] + cp * 28) for l in range(32)]
+        assert wavefronts(ad, 8) == 2
+    for j in range(0, 23, 2):  # mask pairs j, j + 1 of the lane's row pair
+        ad = [8 * (sep32_task(l)[0] * 312 + sep32_task(l)[1] * 26 + j) for l in range(32)]
+        assert wavefronts(ad) == 4
+    for cp in range(16):     # xB writes by the 24 pass-B lanes
+        ad = {l: 16 * (sep32_task(l)[0] * 212 + cp * 13 + sep32_task(l)[1]) for l in range(24)}
+        assert wavefronts_subset(ad) == 3
+    for rp in range(12):     # pass C reads of xB
+        assert wavefronts([16 * ((l >> 4) * 212 + (l & 15) * 13 + rp) for l in range(32)]) == 4
+    xa = {b * 472 + c * 28 + i for b in range(2) for c in range(16) for i in range(24)}
+    xb = {(b * 212 + c * 13 + r) for b in range(2) for c in range(16) for r in range(12)}
+    assert len(xa) == 2 * 16 * 24 and max(xa) < 1680
+    assert len(xb) == 2 * 16 * 12 and 4 * max(xb) + 3 < 1680
+    assert (12 * 26 * 8 // 16) % 8 == 4    # second mask copy 156 chunks on: rows r and r + 8 split banks
+
+
+# N = 16: lane -> (block (l & 3) + 4 (l >> 4), column quad (l >> 2) & 3);
+# pass-B task t (rounds of 32) -> (block t & 7, row pair t >> 3), t < 48.
+# xA words cp*104 + b*12 + i; xB chunks 208 + b*49 + cp*6 + r.
+def sep16_lane(l):
+    return (l & 3) + 4 * (l >> 4), (l >> 2) & 3
+
+
+def test_sep16_accesses_conflict_free():
+    for i in range(16):      # pass A: staged row i, 8 bytes per lane (columns 4q .. 4q+3)
+        ad = [sep16_lane(l)[0] * 32 + 8 * sep16_lane(l)[1] + i * 1024 for l in range(32)]
+        assert wavefronts(ad, 8) == 2
+    for h, t in itertools.product(range(2), range(3)):   # xA writes, column pair 2q + h
+        ad = [4 * ((2 * sep16_lane(l)[1] + h) * 104 + sep16_lane(l)[0] * 12 + 4 * t) for l in range(32)]
+        assert wavefronts(ad) == 4
+    for rd in range(2):
+        tasks = [min(rd * 32 + l, 47) for l in range(32)]
+        for cp in range(8):  # pass B reads of xA
+            assert wavefronts([4 * (cp * 104 + (t & 7) * 12 + 2 * (t >> 3)) for t in tasks], 8) == 2
+            ad = {l: 16 * (208 + (t & 7) * 49 + cp * 6 + (t >> 3)) for l, t in enumerate(tasks)
+                  if rd * 32 + l < 48}
+            assert wavefronts_subset(ad) == (4 if rd == 0 else 2)
+    for h, rp in itertools.product(range(2), range(6)):  # pass C reads of xB
+        ad = [16 * (208 + sep16_lane(l)[0] * 49 + (2 * sep16_lane(l)[1] + h) * 6 + rp) for l in range(32)]
+        assert wavefronts(ad) == 4
+    xa = {cp * 104 + b * 12 + i for cp in range(8) for b in range(8) for i in range(12)}
+    xb = {208 + b * 49 + cp * 6 + r for b in range(8) for cp in range(8) for r in range(6)}
+    assert len(xa) == 8 * 8 * 12 and max(xa) < 832
+    assert len(xb) == 8 * 8 * 6 and min(xb) * 4 >= 832 and 4 * max(xb) + 3 < 832 + 4 * 8 * 49
+
+
+def wavefronts_subset(addrs, width=16):
+    """wavefronts of a 128-bit access by the lanes present in `addrs` (lane -> byte address)"""
+    total = 0
+    for ph in [range(8 * i, 8 * i + 8) for i in range(4)]:
+        banks = {}
+        for lane in ph:
+            if lane not in addrs:
+                continue
+            for w in range(width // 4):
+                word = addrs[lane] // 4 + w
+                banks.setdefault(word % 32, set()).add(word)
+        if banks:
+            total += max(len(s) for s in banks.values())
+    return total
