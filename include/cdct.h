@@ -94,8 +94,9 @@ typedef struct {
 
 /* Create a plan for block size n (8, 16, 32) and a variant; flags is
  * CDCT_CONV_PAPER or CDCT_CONV_TRANSPOSE.  *out receives the plan, which
- * the caller releases with cdct_plan_destroy.  Plans are immutable and may
- * be shared between threads. */
+ * the caller releases with cdct_plan_destroy.  A plan's only mutable state
+ * is its pipeline schedule (cdct_plan_set_tuning); threads may share a plan
+ * as long as none changes its schedule while another uses it. */
 cdct_status cdct_plan_create(int n, int variant, uint32_t flags, cdct_plan* out);
 cdct_status cdct_plan_destroy(cdct_plan plan);
 
@@ -222,7 +223,13 @@ cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, do
  *    capture.
  *  - The scratch is shared by every call on the device: calls that overlap
  *    on the GPU (other streams, other threads) race on it and must be
- *    ordered by the caller.  Nothing in it has to start at zero.
+ *    ordered by the caller.  Nothing in it has to start at zero: every
+ *    partial a call reads is written by the same call, unless a bounded wait
+ *    gives up (cdct_check_device then returns CDCT_ETIMEOUT), in which case
+ *    the unfinished units' partials are written as NaN and psnr_db is NaN.
+ *  - The looked-up address stays valid for the life of the device's primary
+ *    context: no cdct call may follow a cudaDeviceReset of that device in
+ *    the same process.
  *  - No device memory is allocated or freed by this call. */
 cdct_status cdct_fwd_zonal_inv_noalloc(cdct_plan plan, const cdct_image* in, int r, float* recon,
                                        int64_t recon_pitch, int64_t recon_batch_stride, void* kept,
@@ -408,6 +415,21 @@ cdct_status cdct_cnn_adam(float* params, const float* grad, float* m, float* v, 
  * products).  Returns CDCT_ETIMEOUT and clears the record if so,
  * CDCT_OK otherwise.  Outputs of a call that timed out are incomplete. */
 cdct_status cdct_check_device(void* stream);
+
+/* Failure-detection test hook; the paper has no counterpart.  Makes the
+ * library's bounded waits run out on purpose, with no GPU fault and nothing
+ * left in flight, so that a test can check that the time-out is detected and
+ * reported (cdct_check_device) and that the next calls work normally.
+ *   mode 0: off (the default; normal one-second limits).
+ *   bit 0: the fused pipelined kernel arms its staging barriers but issues no
+ *          bulk copy, so every stage wait gives up after `wait_limit_cycles`
+ *          SM cycles; its outputs are then not written.
+ *   bit 1: the training GEMMs issue no tensor-core MMA and no commit, so
+ *          their accumulator wait gives up after `wait_limit_cycles`.
+ * `wait_limit_cycles` must lie in [1000, 2^31] when mode != 0 (ignored
+ * otherwise).  The setting is process-wide and applies to launches made after
+ * the call; CDCT_EINVAL for an invalid mode or limit. */
+cdct_status cdct_set_fault_injection(int mode, int64_t wait_limit_cycles);
 
 /* Host copy of a plan matrix (CDCT_MATRIX_*), computed by running the
  * library's own butterflies on unit vectors.  `out` is host memory of N*N

@@ -29,7 +29,7 @@ EXPORTS = (
     "cdct_rd_create", "cdct_rd_destroy", "cdct_rd_tables", "cdct_rd_region_count", "cdct_rd_search",
     "cdct_cnn_packed_bytes", "cdct_cnn_pack", "cdct_cnn_infer", "cdct_cnn_workspace_size", "cdct_cnn_grad",
     "cdct_cnn_adam", "cdct_rd_search_subset", "cdct_rd_evaluate", "cdct_cnn_select",
-    "cdct_ssim_workspace_size", "cdct_ssim",
+    "cdct_ssim_workspace_size", "cdct_ssim", "cdct_set_fault_injection",
 )
 CNN_PARAMS, CNN_LABELS, CNN_SLOTS = 48241, 17, 4
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cdct_last_error": (ctypes.c_char_p, []),
         "cdct_version": (ctypes.c_char_p, []),
         "cdct_check_device": (ctypes.c_int, [vp]),
+        "cdct_set_fault_injection": (ctypes.c_int, [ctypes.c_int, i64]),
         "cdct_fwd_zonal_inv_noalloc": (ctypes.c_int, [vp, img_p, ctypes.c_int, vp, i64, i64, vp, vp, vp]),
         "cdct_plan_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "cdct_batch_create": (ctypes.c_int, [vp, ctypes.POINTER(CdctBatchImage), ctypes.c_int, ctypes.c_int,
@@ -132,6 +133,16 @@ def lib() -> ctypes.CDLL:
 def check_device(stream=None) -> None:
     """Synchronise the stream; raise if a kernel gave up a bounded wait."""
     check(lib().cdct_check_device(stream_handle(stream)))
+
+
+def device_status(stream=None) -> int:
+    """cdct_check_device's status code (CDCT_OK, or CDCT_ETIMEOUT once after a wait gave up)."""
+    return int(lib().cdct_check_device(stream_handle(stream)))
+
+
+def set_fault_injection(mode: int, wait_limit_cycles: int = 0) -> None:
+    """cdct_set_fault_injection: failure-detection test hook (0 turns it off)."""
+    check(lib().cdct_set_fault_injection(mode, wait_limit_cycles))
 
 
 def check(status: int) -> None:

@@ -3,7 +3,9 @@
 
 #include <cmath>
 #include <cstdint>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <algorithm>
 #include <new>
 #include <string>
@@ -28,6 +30,18 @@ constexpr size_t kNoAllocScratchDoubles = size_t(1) << 17;   // 1 MiB
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 struct cdct_batch_s;
+
+// Failure-detection test hook (cdct_set_fault_injection).
+static std::atomic<int> g_fault_mode{0};
+static std::atomic<long long> g_fault_limit{kDefaultWaitLimit};
+
+namespace cdct {
+int fault_mode(long long* wait_limit) {
+  const int m = g_fault_mode.load();
+  if (wait_limit != nullptr) *wait_limit = m ? g_fault_limit.load() : kDefaultWaitLimit;
+  return m;
+}
+}  // namespace cdct
 
 struct cdct_rd_s {
   int variant;
@@ -74,13 +88,18 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 constexpr int kMaxDevices = 64;
 
-// per-device cache of the SM count and of the error word's address
+// per-device cache of the SM count and of the error word's address; the
+// first call on a device fills it under g_dev_mutex, later calls read it
+// after seeing `ready` (so first calls from several threads do not race)
 struct DeviceInfo {
   int sms = 0;
   int* err = nullptr;
   double* noalloc_scratch = nullptr;   // device address of g_noalloc_scratch
+  std::atomic<bool> ready{false};
+  std::atomic<bool> scratch_ready{false};
 };
 DeviceInfo g_dev[kMaxDevices];
+std::mutex g_dev_mutex;
 
 int device_info(DeviceInfo** out) {
   int dev = 0;
@@ -88,15 +107,19 @@ int device_info(DeviceInfo** out) {
   if (e != cudaSuccess) return static_cast<int>(e);
   if (dev < 0 || dev >= kMaxDevices) return static_cast<int>(cudaErrorInvalidDevice);
   DeviceInfo& d = g_dev[dev];
-  if (d.err == nullptr) {
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return static_cast<int>(e);
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_device_error);
-    if (e != cudaSuccess) return static_cast<int>(e);
-    d.sms = sms;
-    d.err = static_cast<int*>(p);
+  if (!d.ready.load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if (!d.ready.load(std::memory_order_relaxed)) {
+      int sms = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return static_cast<int>(e);
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_device_error);
+      if (e != cudaSuccess) return static_cast<int>(e);
+      d.sms = sms;
+      d.err = static_cast<int*>(p);
+      d.ready.store(true, std::memory_order_release);
+    }
   }
   *out = &d;
   return 0;
@@ -414,7 +437,7 @@ cdct_status cdct_fwd_zonal_inv(cdct_plan plan, const cdct_image* in, int r, floa
     pa.units_per_row = static_cast<int>(units_per_row(plan, a));
     pa.units_per_img = static_cast<long long>(pa.units_per_row) * a.nby;
     pa.total_units = pa.units_per_img * in->batch;
-    pa.wait_limit = 1ll << 31;   // about one second of SM clock
+    pa.drop_copies = fault_mode(&pa.wait_limit) & 1;
     pa.div_img = make_fastdiv(static_cast<uint32_t>(pa.units_per_img));
     pa.div_row = make_fastdiv(static_cast<uint32_t>(pa.units_per_row));
     parts_per_img = pa.units_per_img * (kThreads / 32);   // one partial per warp and unit
@@ -474,11 +497,15 @@ cdct_status cdct_fwd_zonal_inv_noalloc(cdct_plan plan, const cdct_image* in, int
   if (e != cudaSuccess) return cuda_fail(static_cast<int>(e), "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(CDCT_EUNSUPPORTED, "device ordinal out of range");
   DeviceInfo& d = g_dev[dev];
-  if (d.noalloc_scratch == nullptr) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(static_cast<int>(e), "cudaGetSymbolAddress(scratch)");
-    d.noalloc_scratch = static_cast<double*>(ptr);
+  if (!d.scratch_ready.load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if (!d.scratch_ready.load(std::memory_order_relaxed)) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(static_cast<int>(e), "cudaGetSymbolAddress(scratch)");
+      d.noalloc_scratch = static_cast<double*>(ptr);
+      d.scratch_ready.store(true, std::memory_order_release);
+    }
   }
   // every partial a call reads is written by the same call, so the scratch
   // needs no clearing between calls
@@ -640,7 +667,7 @@ cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, do
   const int nsub = (plan->n / 8) * (plan->n / 8);
   for (int q = 0; q < 16; ++q) a.slab_mask[q] = q < nsub ? sub_mask(plan->n, r, q) : 0ull;
   pa.total_units = batch->total_units;
-  pa.wait_limit = 1ll << 31;
+  pa.drop_copies = fault_mode(&pa.wait_limit) & 1;
   pa.err = di->err;
   const BatchImage* images = static_cast<const BatchImage*>(device_table);
   const long long* unit_prefix =
@@ -652,6 +679,15 @@ cdct_status cdct_batch_fzi(cdct_batch batch, const void* device_table, int r, do
     rc = launch_finalize_table(a.partial, unit_prefix, images, batch->n_images, kThreads / 32, psnr_db, stream);
     if (rc) return cuda_fail(rc, "batch psnr launch");
   }
+  return CDCT_OK;
+}
+
+cdct_status cdct_set_fault_injection(int mode, int64_t wait_limit_cycles) {
+  if (mode < 0 || mode > 3) return fail(CDCT_EINVAL, "fault injection mode must be 0..3");
+  if (mode != 0 && (wait_limit_cycles < 1000 || wait_limit_cycles > kDefaultWaitLimit))
+    return fail(CDCT_EINVAL, "fault injection wait limit must be in [1000, 2^31] cycles");
+  g_fault_limit.store(mode ? wait_limit_cycles : kDefaultWaitLimit);
+  g_fault_mode.store(mode);
   return CDCT_OK;
 }
 

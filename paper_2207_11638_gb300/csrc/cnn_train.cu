@@ -48,13 +48,15 @@ using namespace cnn;
 //      bias + ReLU -> bf16.
 // ---------------------------------------------------------------------------
 constexpr int kGemmThreads = 128;
-constexpr long long kTcWaitLimit = 1ll << 31;   // SM cycles (~1 s) before a wait gives up
 
+// `skip_mma` (failure-detection test): issue neither the MMAs nor their
+// commit, so that the accumulator wait runs out with nothing in flight.
 template <int BN, bool RELU_BF16>
 __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const uint16_t* __restrict__ A,
                                                                const uint16_t* __restrict__ B, long long M, int N,
                                                                int K, const float* __restrict__ bias,
-                                                               void* __restrict__ C, int* __restrict__ err) {
+                                                               void* __restrict__ C, int* __restrict__ err,
+                                                               long long wait_limit, int skip_mma) {
   extern __shared__ __align__(1024) unsigned char smg[];
   __shared__ __align__(8) uint64_t done;
   __shared__ uint32_t tmem_base;
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const uint16_t* _
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  if (tid == 0) {
+  if (tid == 0 && !skip_mma) {
     constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
     const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
     for (int kk = 0; kk < K / 16; ++kk)
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const uint16_t* _
                 kk > 0 ? 1u : 0u);
     umma_commit(&done);
   }
-  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&done, 0, kTcWaitLimit));
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&done, 0, wait_limit));
   tc_fence_after();
   if (ok) {
     const long long row = m0 + warp * 32 + lane;
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const uint16_t* _
   } else if (tid == 0) {
     atomicOr(err, 2);
     // the MMAs may still be running: wait for them (bounded) before freeing their memory
-    (void)mbar_wait_bounded(&done, 0, kTcWaitLimit);
+    (void)mbar_wait_bounded(&done, 0, wait_limit);
   }
   tc_fence_before();
   __syncthreads();
@@ -138,7 +140,9 @@ int gemm_launch_t(const uint16_t* A, const uint16_t* B, long long M, int N, int 
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return static_cast<int>(e);
   dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>(N / BN));
-  kern<<<grid, kGemmThreads, smem, s>>>(A, B, M, N, K, bias, C, err);
+  long long limit = kDefaultWaitLimit;
+  const int mode = fault_mode(&limit);
+  kern<<<grid, kGemmThreads, smem, s>>>(A, B, M, N, K, bias, C, err, limit, (mode & 2) ? 1 : 0);
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -97,7 +97,13 @@ struct PipeArgs {
   const UnitDesc* unit_map;  // descriptor-table batches: one record per work unit (null: uniform batch)
   int* err;                // device error word (bit 0: a bulk copy never landed)
   long long wait_limit;    // SM cycles before a stage wait gives up
+  int drop_copies;         // failure-detection test: arm the stage barriers but issue no copy
 };
+
+// Failure-detection test hook (cdct_set_fault_injection): the current mode
+// bits and the wait limit, in SM cycles, the kernels use while it is set.
+constexpr long long kDefaultWaitLimit = 1ll << 31;   // about one second of SM clock
+int fault_mode(long long* wait_limit);
 
 // Tuning of the pipelined kernel: staging depth (0 = default for N) and
 // resident CTAs per SM used for the grid (0 = as many as fit).

@@ -815,6 +815,11 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES, BODY>::value) fzi
     // the record of the unit this stage takes after u
     const long long un = u + STAGES * G_;
     const uint32_t rec_bytes = (TABLE && un < pa.total_units) ? static_cast<uint32_t>(sizeof(UnitDesc)) : 0u;
+    if (pa.drop_copies) {          // failure-detection test: the stage's phase can never complete
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], 16u);
+      __syncwarp();
+      return;
+    }
     if (d.pack == 1) {
       if (lane == 0) {
         if constexpr (TABLE) usrc[s] = d;
@@ -867,7 +872,8 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES, BODY>::value) fzi
     if (u >= pa.total_units) break;
     const int s = it % STAGES;
     const uint32_t parity = static_cast<uint32_t>((it / STAGES) & 1);
-    if (!mbar_wait_bounded(&full[s], parity, pa.wait_limit)) { failed = true; break; }
+    const bool landed = mbar_wait_bounded(&full[s], parity, pa.wait_limit);
+    if (!__all_sync(0xffffffffu, landed)) { failed = true; break; }   // the warp stops as one
     const unsigned char* stage = smem + s * PG::STAGE_BYTES;
 
     UnitSrc<InT> d;
@@ -938,6 +944,11 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<N, STAGES, BODY>::value) fzi
 
   if (failed) {
     if (lane == 0) atomicOr(pa.err, 1);
+    // the units this warp leaves unfinished get NaN partials, so that a PSNR
+    // reduced from them shows the failure instead of stale values
+    if (a.partial != nullptr && lane == 0)
+      for (long long uk = blockIdx.x + static_cast<long long>(it) * G_; uk < pa.total_units; uk += G_)
+        a.partial[uk * NW + warp] = __longlong_as_double(0x7FF8000000000000ll);
     // wait (bounded) for copies that may still be landing in this CTA's
     // stages, so that none writes shared memory after the CTA exits
     for (int k = 0; k < STAGES; ++k) {

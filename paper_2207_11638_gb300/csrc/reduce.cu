@@ -12,7 +12,8 @@ namespace {
 constexpr int kFinalThreads = 256;
 constexpr int kPsnrRows = 4;           // image rows per CTA of the standalone error kernel
 
-// psnr[img] = 10 log10(255^2 npix / SSE), +inf when SSE = 0 (Sec. 5.1 PSNR).
+// psnr[img] = 10 log10(255^2 npix / SSE), +inf when SSE = 0 (Sec. 5.1 PSNR);
+// NaN partials (a kernel that gave up a bounded wait) give NaN.
 __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const FinalArgs a) {
   __shared__ double red[kFinalThreads];
   const int img = blockIdx.x;
@@ -28,8 +29,8 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const FinalArgs
   if (threadIdx.x == 0) {
     const double sse = red[0];
     if (a.sse != nullptr) a.sse[img] = sse;
-    a.psnr[img] = (sse > 0.0) ? 10.0 * log10(255.0 * 255.0 * static_cast<double>(a.npix) / sse)
-                              : static_cast<double>(INFINITY);
+    a.psnr[img] = (sse == 0.0) ? static_cast<double>(INFINITY)
+                               : 10.0 * log10(255.0 * 255.0 * static_cast<double>(a.npix) / sse);
   }
 }
 
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_table_kernel(const dou
   if (threadIdx.x == 0) {
     const double sse = red[0];
     const double npix = static_cast<double>(images[img].width) * images[img].height;
-    psnr[img] = (sse > 0.0) ? 10.0 * log10(255.0 * 255.0 * npix / sse) : static_cast<double>(INFINITY);
+    psnr[img] = (sse == 0.0) ? static_cast<double>(INFINITY) : 10.0 * log10(255.0 * 255.0 * npix / sse);
   }
 }
 

@@ -107,3 +107,12 @@ def test_block_count_and_workspace():
         ws = ctypes.c_size_t()
         assert lib.cdct_workspace_size(p.handle, ctypes.byref(d), ctypes.byref(ws)) == 0
         assert ws.value >= 8 * batch and ws.value % 8 == 0
+
+
+def test_fault_injection_hook_argument_checks():
+    """The failure-detection test hook validates its arguments on the host."""
+    for mode, limit in ((4, 1 << 21), (-1, 1 << 21), (1, 10), (1, 1 << 40)):
+        with pytest.raises(b.CdctError):
+            b.set_fault_injection(mode, limit)
+    b.set_fault_injection(1, 1 << 21)
+    b.set_fault_injection(0)

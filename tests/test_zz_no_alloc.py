@@ -62,12 +62,15 @@ def test_noalloc_matches_workspace_call_twice(n, variant, dtype, shape, r):
     img = _case(dtype, shape, seed=n + r)
     other = _case(dtype, (1, 64, 64), seed=99)
     want = plan.fwd_zonal_inv(img, r)
+    want_other = plan.fwd_zonal_inv(other, r)
     for _ in range(2):                      # the scratch keeps the last call's contents
         got = b.fwd_zonal_inv_noalloc(plan, img, r)
         torch.cuda.synchronize()
         _same(got, want)
-        b.fwd_zonal_inv_noalloc(plan, other, r)   # a different call in between
+        # a smaller call in between, which finds the larger call's partials in the scratch
+        got_other = b.fwd_zonal_inv_noalloc(plan, other, r)
         torch.cuda.synchronize()
+        _same(got_other, want_other)
     b.check_device()
 
 
