@@ -54,14 +54,16 @@ def parse():
                     help="run every transform with its default pipeline schedule")
     ap.add_argument("--pass", dest="pass_", default="N32_hat",
                     help="pass workload: the transform, N{8,16,32}_{tilde,hat}")
-    ap.add_argument("--workload", choices=("frames", "uneven", "rd", "learned", "pipeline4k", "pass"), default="frames",
+    ap.add_argument("--workload", choices=("frames", "uneven", "rd", "learned", "pipeline4k", "pass", "cnn_infer"),
+                    default="frames",
                     help="frames: 64 1080p 4:2:0 residual frames (default); uneven: 4096 u8 images of "
                          "log-uniform sizes in one persistent launch per pass, CUDA-graph replay; rd: "
                          "exhaustive RD quadtree search over 200k 32x32 residual regions at q = 8, 16, 32; "
                          "learned: train the CNN size selector on the search's labels, then time CNN-chosen "
                          "quadtrees + coding against exhaustive search + coding on the same regions; pipeline4k: "
                          "the trained selector against the search on 64 3840x2160 4:2:0 residual frames; pass: one "
-                         "fused pass (--pass) over the luma planes of --frames frames, a small case for profiling")
+                         "fused pass (--pass) over the luma planes of --frames frames, a small case for profiling; "
+                         "cnn_infer: the selector's inference kernel alone on --regions regions (seeded weights)")
     ap.add_argument("--epochs", type=int, default=16, help="learned workload: training epochs")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned workload: peak Adam learning rate")
     ap.add_argument("--mu", type=float, default=300.0, help="learned workload: weight of the RD-regret loss term")
@@ -1258,6 +1260,46 @@ def run_pass(args):
     return 0
 
 
+def run_cnn_infer(args):
+    """The selector's inference kernel alone (3 quantiser slots, labels and
+    margins out) on the first --regions 32 x 32 regions of the region
+    workload, with seeded He-normal weights: the case the inference profiles
+    in profiles/ capture.  Prints one JSON line with the time per call and the
+    tensor-core rate."""
+    import torch
+    from paper_2207_11638_gb300 import binding as b
+    from paper_2207_11638_gb300 import synth
+
+    torch.cuda.set_device(dist_env()[2])
+    regs = torch.from_numpy(synth.residual_regions_32(args.regions, seed=4)).cuda()
+    net = b.Cnn(torch.from_numpy(synth.cnn_init_params(0)).cuda())
+    net.pack()
+    slots = (0, 1, 2)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        net.infer(regs, slots, margin=True)
+    torch.cuda.synchronize()
+    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_.record(stream)
+    for _ in range(args.steps):
+        net.infer(regs, slots, margin=True)
+    e_.record(stream)
+    torch.cuda.synchronize()
+    b.check_device()
+    ms = s_.elapsed_time(e_) / args.steps
+    flop = (CNN_FLOP_PER_REGION + len(slots) * CNN_HEAD_FLOP_PER_SLOT) * args.regions
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    tf = flop / (ms / 1e3) / 1e12
+    print(json.dumps({"workload": f"cnn_infer over {args.regions} regions, 3 slots", "ms_per_call": ms,
+                      "regions_per_ms": args.regions / ms, "TFLOP_s": tf, "frac_of_bf16_peak": tf / peak}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1272,6 +1314,8 @@ def main():
         return run_pipeline4k(args)
     if args.workload == "pass":
         return run_pass(args)
+    if args.workload == "cnn_infer":
+        return run_cnn_infer(args)
     return run_ours(args)
 
 

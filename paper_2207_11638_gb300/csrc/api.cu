@@ -884,7 +884,7 @@ cdct_status cdct_cnn_infer(const void* packed, const cdct_image* in, const int32
   int sl[CDCT_CNN_SLOTS];
   for (int k = 0; k < n_slots; ++k) sl[k] = slots[k];
   rc = cnn_infer_launch(packed, in->data, in->dtype, in->pitch, in->batch_stride, in->width, in->height, in->batch,
-                        sl, n_slots, labels, logits, margin, di->sms, stream);
+                        sl, n_slots, labels, logits, margin, di->sms, di->err, stream);
   return rc ? cuda_fail(rc, "cnn inference launch") : CDCT_OK;
 }
 

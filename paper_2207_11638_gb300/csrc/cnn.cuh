@@ -59,7 +59,7 @@ static_assert(kParams == 48241, "parameter count");
 int cnn_pack_launch(const float* params, void* packed, void* stream);
 int cnn_infer_launch(const void* packed, const void* in, int dtype, long long pitch, long long bstride, int width,
                      int height, int batch, const int* slots, int n_slots, unsigned char* labels, float* logits,
-                     float* margin, int num_sms, void* stream);
+                     float* margin, int num_sms, int* err, void* stream);
 int cnn_select_launch(const float* margin, long long n, int ns, float threshold, long long* idx, long long* count,
                       int num_sms, void* stream);
 // launchers (cnn_train.cu)
