@@ -1090,7 +1090,7 @@ def run_learned(args):
                      "epoch_end_losses": [round(float(x.cpu()[0]), 4) for x in losses],
                      "heldout_label_accuracy": round(acc, 4)},
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                     "traffic": None, "kernel": "cnn_infer_kernel (fused conv trunk + FC head, mma.sync bf16)",
+                     "traffic": None, "kernel": "cnn_infer_tc_kernel (conv trunk on tcgen05, FC head on warp-level MMA)",
                      "flop_per_region": CNN_FLOP_PER_REGION + len(slots) * CNN_HEAD_FLOP_PER_SLOT,
                      "peak_kind": kind},
         # the decision's oracle baseline: the exhaustive search the selector replaces

@@ -336,7 +336,7 @@ cdct_status cdct_rd_evaluate(cdct_rd rd, const cdct_image* in, const int32_t* q,
  * Precision: weights (W_l, Wf1, Wq, Wf2) are used as bfloat16 copies (round
  * to nearest even) of float32 master weights; biases stay float32; every
  * stored activation (a_l, g) is bfloat16; products accumulate in float32 on
- * the tensor cores (mma.sync m16n8k16).
+ * the tensor cores (the order of the sums is not fixed).
  *
  * Parameters: one float32 vector of CDCT_CNN_PARAMS values, in this order:
  *   W1 [16][3][3][1]   b1 [16]   W2 [32][3][3][16]  b2 [32]
@@ -362,7 +362,10 @@ cdct_status cdct_cnn_pack(const float* params, void* packed, void* stream);
  *   labels  [n_slots][n_regions] uint8 (required)
  *   logits  [n_slots][n_regions][17] float, or NULL
  *   margin  [n_slots][n_regions] float: best minus second-best logit (the
- *           selector's confidence; 0 on ties), or NULL */
+ *           selector's confidence; 0 on ties), or NULL
+ * CDCT_EINVAL for 2^31 or more regions in one call (split the batch).  A
+ * tensor-core wait that runs out is reported by cdct_check_device
+ * (CDCT_ETIMEOUT); the outputs of that call are then incomplete. */
 cdct_status cdct_cnn_infer(const void* packed, const cdct_image* in, const int32_t* slots, int32_t n_slots,
                            uint8_t* labels, float* logits, float* margin, void* stream);
 

@@ -877,6 +877,7 @@ cdct_status cdct_cnn_infer(const void* packed, const cdct_image* in, const int32
   st = check_slots(slots, n_slots);
   if (st != CDCT_OK) return st;
   if (labels == nullptr) return fail(CDCT_EINVAL, "null labels pointer");
+  if (n_regions >= (int64_t{1} << 31)) return fail(CDCT_EINVAL, "more than 2^31 - 1 regions in one call");
   if (n_regions == 0) return CDCT_OK;
   DeviceInfo* di = nullptr;
   int rc = device_info(&di);

@@ -28,7 +28,7 @@ namespace {
 using namespace cnn;
 
 constexpr int kFeatPitch = 520;                 // bf16 per feature row (512 + 8)
-constexpr int kF2Pitch = kHidden + 1;            // Wf2 row pitch in shared memory (floats)
+constexpr int kF2Pitch = kHidden + 4;            // Wf2 row pitch in shared memory (floats; 16-byte rows)
 constexpr int kHeadBytes = ((kHidden + kHidden * kSlots + kLabels * kF2Pitch + kLabels) * 4 + 15) / 16 * 16;
 
 struct InferArgs {

@@ -28,14 +28,17 @@
 //       + (C & 1) * 144 + (C >> 1) * 16
 //     for padded row R, column C (0..17), so that for every tap the 8
 //     windows of a core matrix are 16 B apart and consecutive core matrices
-//     288 B apart.  Window pixel g = (py, px) and tap (dy, dx) read the map at
-//     (2 v + py + dy, 2 u + px + dx): 4 groups x 9 taps = 36 MMAs of N = 32,
-//     K = 16 (lbo = a plane of 8 channels), accumulating into column group g.
+//     288 B apart.  A window's receptive field is 4 x 4 pixels: one MMA per
+//     offset (ry, rx) in it reads the map at (2 v + ry, 2 u + rx) with K = 16
+//     (lbo = a plane of 8 channels) and N = 128 = window pixel g x 32
+//     channels, whose B operand holds W2's tap (ry - py, rx - px) for pixel g
+//     = (py, px), or zeros where that is not a tap: 16 MMAs per pair.
 //   conv3 (32 -> 32, 8 x 8 px): pixel-tiled, as its windows (2 x 16 per pair)
 //     fill no tile: the pooled conv2 maps of the pair sit side by side in a
 //     [4][10][20][8] map; M = 128 covers both regions, core matrix
 //     k = 2 i + s (output row i of region s) at 160 k + (dy*20 + dx)*16:
-//     sbo = 160 B, lbo = 3200 B; 18 MMAs (taps x channel halves), N = 32.
+//     sbo = 160 B, lbo = 3200 B; 18 MMAs (taps x channel halves), N = 32,
+//     in three independent partial sums.
 //     The pool is a butterfly between lanes: partners trade halves of their
 //     channels and keep the maximum, twice.
 // Bias and ReLU follow the maximum (both commute with it); each pooled map is
@@ -43,22 +46,32 @@
 // Weights (B operands) are repacked once per CTA into the same layout (128 B
 // apart along K, 256 B along N).
 //
-// A CTA of 4 warps runs 16 regions per iteration, a pair at a time: both
-// regions' conv1 tiles are issued together (each committed to its own
-// mbarrier, so the epilogue of one tile overlaps the MMAs of the next), then
-// the pair's conv2 and conv3; FC1 (warp-level MMA) and the per-slot head run
-// once over the 16 regions.  The next pair's pixels are loaded into
-// registers while the current pair computes.  Two CTAs share an SM.  Every
-// tensor-core wait is bounded; a CTA that gives up records the error word,
-// waits (bounded) for its outstanding MMAs, frees its tensor memory and stops.
+// One CTA per SM (all 512 tensor-memory columns), warp-specialised, runs a
+// software pipeline over pairs of regions:
+//   4 staging warps load pair k + 1's pixels while expanding pair k into one
+//     of two expanded-map slots;
+//   1 MMA warp issues, in iteration k, conv1 of pair k, conv2 of pair k - 1
+//     and conv3 of pair k - 2 (activation maps double-buffered), each as soon
+//     as its inputs are written and its accumulators drained;
+//   8 epilogue warps drain the accumulators in completion order (warps w and
+//     w + 4 read the same tensor-memory lanes and split the channels) and run
+//     FC1 and the per-slot head every 8 pairs.
+// The roles meet on mbarriers only.  The tensor core's cost here is set by
+// the A operand: an M = 128, K = 16 MMA reads 4 KB of shared memory whatever
+// N is (up to 128), which is why conv2 uses N = 128.  Every wait is bounded;
+// a role that gives up raises a shared abort flag that ends the others' waits,
+// the MMA warp waits (bounded) for its outstanding MMAs, and the CTA records
+// the error word and frees its tensor memory.
 
-constexpr int kWarpsT = 4;
+constexpr int kWarpsT = 8;                       // epilogue warps (two per tensor-memory lane quadrant)
 constexpr int kThreadsT = 32 * kWarpsT;
-constexpr int kGroupT = 16;                      // regions per CTA iteration (FC1 batch)
-constexpr uint32_t kTmemColsT = 256;
-// tensor-memory columns: conv1 of the pair's regions 0..127 and 128..255;
-// then conv2 of the pair 0..127 and conv3 128..159
-constexpr uint32_t kC1Col0 = 0, kC1Col1 = 128, kC2Col = 0, kC3Col = 128;
+constexpr int kIssuerWarp = kWarpsT, kProducerWarp0 = kWarpsT + 1, kProducerWarps = 4;
+constexpr int kBlockT = kThreadsT + 32 * (1 + kProducerWarps);   // + the MMA-issuing warp and the staging warps
+constexpr int kGroupT = 16;                      // regions per FC1 batch
+constexpr int kPairsT = kGroupT / 2;
+constexpr uint32_t kTmemColsT = 512;
+// tensor-memory columns: conv1 of a pair (4 tiles of 64), conv2 of a pair, conv3 of a pair (3 partial sums)
+constexpr uint32_t kC1Col = 0, kC2Col = 256, kC3Col = 384;
 constexpr int kERow = 16 * 16;                   // bytes per row of the expanded map
 constexpr int kEBytes = 17 * kERow;              // E[17][16] x 16 B
 // conv2 input map of a pair (parity-split, see above)
@@ -71,24 +84,26 @@ constexpr int kAct1T = 2 * kA1Plane;
 constexpr int kA3Plane = 10 * 20 * 16;           // bytes per channel plane of the stacked conv2 map
 constexpr int kAct2T = 4 * kA3Plane;             // [4][10][20][8] bf16
 
-// shared-memory layout (bytes)
+// shared-memory layout (bytes); the activation maps are double-buffered
 constexpr int kTCB = 0;                                     // biases b1 b2 b3 [80] float
 constexpr int kTB1 = 384;                                   // conv1 B operand [64 x 16]
-constexpr int kTB2 = kTB1 + 2048;                           // conv2 B operands [9 taps][1024 B]
-constexpr int kTB3 = kTB2 + 9 * 1024;                       // conv3 B operands [18 slabs][1024 B]
-constexpr int kTHead = kTB3 + 18 * 1024;                    // fb1, Wq, Wf2 (65-float rows), fb2
-constexpr int kTE = (kTHead + kHeadBytes + 127) / 128 * 128;   // expanded maps of the pair
-constexpr int kTAct1 = kTE + 2 * kEBytes;                   // conv2 input map (also the head's hidden values)
-constexpr int kTAct2 = kTAct1 + kAct1T;                     // conv3 input map of the pair
-constexpr int kTFeat = kTAct2 + kAct2T;                     // features [16][520] bf16
-constexpr int kTU = kTFeat + kGroupT * kFeatPitch * 2;      // FC1 outputs [16][64] float
-constexpr int kTLogit = kTU + kGroupT * kHidden * 4;        // logits [16][4][17] float
+constexpr int kTB2 = kTB1 + 2048;                           // conv2 B operands [16 offsets][4096 B]
+constexpr int kTB3 = kTB2 + 16 * 4096;                      // conv3 B operands [18 slabs][1024 B]
+constexpr int kTHead = kTB3 + 18 * 1024;                    // fb1, Wq, Wf2 (68-float rows), fb2
+constexpr int kTE = (kTHead + kHeadBytes + 127) / 128 * 128;   // expanded maps [2 slots][2 regions]
+constexpr int kTAct1 = kTE + 4 * kEBytes;                   // conv2 input maps [2]
+constexpr int kTAct2 = kTAct1 + 2 * kAct1T;                 // conv3 input maps [2]
+constexpr int kTFeat = kTAct2 + 2 * kAct2T;                 // features [16][520] bf16
+constexpr int kHPitch = kHidden + 8;                        // bf16 per row of the hidden values and of Wf2
+constexpr int kTU = kTFeat + kGroupT * kFeatPitch * 2;      // FC1 partial outputs [2 K halves][16][64] float
+constexpr int kTG = kTU + 2 * kGroupT * kHidden * 4;        // hidden values [16 regions x 4 slots][72] bf16
+constexpr int kTW2 = kTG + kGroupT * kSlots * kHPitch * 2;  // Wf2 [24 labels (17 + zero rows)][72] bf16
+constexpr int kTLogit = kTW2 + 24 * kHPitch * 2;            // logits [16][4][17] float
 constexpr int kSmemT = kTLogit + kGroupT * kSlots * kLabels * 4;
 static_assert(kTB1 % 128 == 0 && kTB2 % 128 == 0 && kTE % 128 == 0 && kTAct1 % 128 == 0 && kTAct2 % 128 == 0 &&
-              kTFeat % 16 == 0 && kTU % 16 == 0, "alignment");
+              kTFeat % 16 == 0 && kTU % 16 == 0 && kTG % 16 == 0 && kTW2 % 16 == 0, "alignment");
 static_assert(kRP == 2 * kRS, "core matrix i = 2 v + s is kRS * i bytes from window row 0");
-static_assert(kGroupT * kSlots * kHidden * 4 <= kAct1T, "the head's hidden values fit the conv2 input map");
-static_assert(2 * (kSmemT + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(kSmemT + 1024 <= 227 * 1024, "one CTA per SM");
 
 // byte offset of padded pixel (R, C) of region s, channel plane p, in the conv2 input map
 __device__ __forceinline__ int a1_off(int s, int p, int R, int C) {
@@ -101,7 +116,9 @@ __device__ __forceinline__ int b_off(int n, int k) { return (k >> 3) * 128 + (n 
 
 //   conv1 (n, k), n = 16 g + o for window pixel g = 2 py + px, k = 8 (ry / 2) + 2 rx + ry % 2 for the
 //     receptive-field pixel (ry, rx) in 0..3: W1[o][ry - py][rx - px] where both offsets are in 0..2, else 0
-//   conv2 tap t: (o, c) = W2[o][t * 16 + c];  conv3 slab 2t + h: (o, c) = W3[o][t * 32 + 16 h + c]
+//   conv2 offset (ry, rx) in 0..3: (n, c), n = 32 g + o for window pixel g = 2 py + px:
+//     W2[o][((ry - py) * 3 + rx - px) * 16 + c] where both offsets are in 0..2, else 0
+//   conv3 slab 2t + h: (o, c) = W3[o][t * 32 + 16 h + c]
 __device__ __forceinline__ void pack_b_operands(const unsigned char* packed, unsigned char* sm, int tid) {
   const uint16_t* w1 = reinterpret_cast<const uint16_t*>(packed + kPkW1);
   const uint16_t* w2 = reinterpret_cast<const uint16_t*>(packed + kPkW2);
@@ -113,9 +130,12 @@ __device__ __forceinline__ void pack_b_operands(const unsigned char* packed, uns
     const bool in = dy >= 0 && dy <= 2 && dx >= 0 && dx <= 2;
     reinterpret_cast<uint16_t*>(sm + kTB1 + b_off(n, k))[0] = in ? w1[o * kW1Pitch + dy * 3 + dx] : static_cast<uint16_t>(0);
   }
-  for (int i = tid; i < 9 * 32 * 16; i += kThreadsT) {
-    const int t = i >> 9, o = (i >> 4) & 31, c = i & 15;
-    reinterpret_cast<uint16_t*>(sm + kTB2 + t * 1024 + b_off(o, c))[0] = w2[o * kW2Pitch + t * 16 + c];
+  for (int i = tid; i < 16 * 128 * 16; i += kThreadsT) {
+    const int off = i >> 11, n = (i >> 4) & 127, c = i & 15, g = n >> 5, o = n & 31;
+    const int dy = (off >> 2) - (g >> 1), dx = (off & 3) - (g & 1);
+    const bool in = dy >= 0 && dy <= 2 && dx >= 0 && dx <= 2;
+    reinterpret_cast<uint16_t*>(sm + kTB2 + off * 4096 + b_off(n, c))[0] =
+        in ? w2[o * kW2Pitch + (dy * 3 + dx) * 16 + c] : static_cast<uint16_t>(0);
   }
   for (int i = tid; i < 18 * 32 * 16; i += kThreadsT) {
     const int sl = i >> 9, o = (i >> 4) & 31, c = i & 15;
@@ -124,43 +144,46 @@ __device__ __forceinline__ void pack_b_operands(const unsigned char* packed, uns
   }
 }
 
-// The input rows of region `reg` that warp `warp` expands: for row pairs
-// j = warp + 4k <= 16 (k < 5), the padded rows 2j and 2j + 1, i.e. input rows
-// 2j - 1 and 2j (replicated beyond the image, zero outside the region), at the
-// lane's column (replicated beyond the image).  Kept as raw integers and
-// loaded one pair of regions ahead, so that their latency overlaps the
-// previous pair's work.
+// Staging is split over four warps: warp p expands rows j of region p / 2's
+// expanded map with j in [0, 9) for even p, [9, 17) for odd p, from input
+// rows 2j - 1 and 2j (17 and 16 rows; replicated beyond the image, zero
+// outside the region) at the lane's column (replicated beyond the image).
+// The pixels are kept as raw integers and loaded one pair of regions ahead.
+constexpr int kStageRows = 17;
 template <typename InT>
-__device__ __forceinline__ void load_region_rows(const InferArgs& a, long long reg, int warp, int lane, int (&px)[10]) {
-  const int img = static_cast<int>(reg / a.tiles_per_img);
-  const int t = static_cast<int>(reg - static_cast<long long>(img) * a.tiles_per_img);
-  const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+__device__ __forceinline__ void load_half_region(const InferArgs& a, long long reg, int half, int lane,
+                                                 int (&px)[kStageRows]) {
+  const unsigned r32 = static_cast<unsigned>(reg);          // below 2^31 (checked by the caller)
+  const unsigned img = r32 / static_cast<unsigned>(a.tiles_per_img);
+  const unsigned t = r32 - img * static_cast<unsigned>(a.tiles_per_img);
+  const int ty = static_cast<int>(t / static_cast<unsigned>(a.tiles_x)), tx = static_cast<int>(t) - ty * a.tiles_x;
   const int y0 = ty * 32, x0 = tx * 32;
   const int vrows = min(32, a.height - y0), vcols = min(32, a.width - x0);
-  const InT* src = static_cast<const InT*>(a.in) + img * a.bstride + x0 + min(lane, vcols - 1);
+  const InT* src = static_cast<const InT*>(a.in) + static_cast<long long>(img) * a.bstride + x0 + min(lane, vcols - 1);
+  // half 0: input rows 0..16 (j = 0..8 use rows -1..16); half 1: rows 17..31 (j = 9..16 use rows 17..32)
+  const int r0 = half ? 17 : 0, nr = half ? 15 : 17;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int j = warp + 4 * k;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int r = 2 * j - 1 + h;                       // input row of padded row 2j + h
-      px[2 * k + h] = (j <= 16 && r >= 0 && r < 32) ? static_cast<int>(src[(y0 + min(r, vrows - 1)) * a.pitch]) : 0;
-    }
-  }
+  for (int i = 0; i < kStageRows; ++i)
+    px[i] = i < nr ? static_cast<int>(src[(y0 + min(r0 + i, vrows - 1)) * a.pitch]) : 0;
 }
 
-// The expanded map E from the loaded rows.  P = bf16(input / 64) (exact for
-// |input| <= 255); the lane of input column x holds the word (P[2j][x + 1],
-// P[2j + 1][x + 1]), and entry E[j][u] gathers the words of padded columns
-// 2u .. 2u + 3, i.e. of lanes 2u - 1 .. 2u + 2 (zero beyond the region).
-__device__ __forceinline__ void store_expanded(const int (&px)[10], unsigned char* e, int warp, int lane) {
+// Rows j of the expanded map E of a region from the loaded pixels (half 0:
+// j = 0..8; half 1: j = 9..16).  P = bf16(input / 64) (exact for |input| <=
+// 255) with a zero border; the lane of input column x forms the word
+// (P[2j][x + 1], P[2j + 1][x + 1]) = (input row 2j - 1, row 2j), and entry
+// E[j][u] gathers the words of padded columns 2u .. 2u + 3, i.e. of lanes
+// 2u - 1 .. 2u + 2 (zero beyond the region).
+__device__ __forceinline__ void store_half_expanded(const int (&px)[kStageRows], int half, unsigned char* e, int lane) {
   const int u = lane & 15;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int j = warp + 4 * k;
-    if (j > 16) break;                                     // warp-uniform
-    const uint32_t w = bf16_bits(static_cast<float>(px[2 * k]) * 0.015625f) |
-                       (bf16_bits(static_cast<float>(px[2 * k + 1]) * 0.015625f) << 16);
+  for (int i = 0; i < 9; ++i) {
+    if (half && i == 8) break;
+    const int j = half ? 9 + i : i;
+    // input row 2j - 1 is px[2j - 1 - r0], row 2j is px[2j - r0] (r0 = 0 or 17)
+    const int lo_i = half ? 2 * i : 2 * i - 1, hi_i = half ? 2 * i + 1 : 2 * i;
+    const float lo = lo_i >= 0 ? static_cast<float>(px[lo_i]) : 0.f;
+    const float hi = (half && i == 7) ? 0.f : static_cast<float>(px[hi_i]);
+    const uint32_t w = bf16_bits(lo * 0.015625f) | (bf16_bits(hi * 0.015625f) << 16);
     uint32_t q0 = __shfl_sync(0xffffffffu, w, (2 * u + 31) & 31), q1 = __shfl_sync(0xffffffffu, w, 2 * u);
     uint32_t q2 = __shfl_sync(0xffffffffu, w, 2 * u + 1), q3 = __shfl_sync(0xffffffffu, w, (2 * u + 2) & 31);
     if (u == 0) q0 = 0u;
@@ -169,23 +192,20 @@ __device__ __forceinline__ void store_expanded(const int (&px)[10], unsigned cha
   }
 }
 
-// 16 float32 columns of the warp's 32 tensor-memory lanes, without waiting
-// (tmem_wait_ld() before use)
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// 8 float32 columns of the warp's 32 tensor-memory lanes, without waiting
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 // wait for this thread's tensor-memory loads; tied to the loaded registers so
 // that no use of them moves above the wait
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[16], uint32_t (&b)[16]) {
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[8], uint32_t (&b)[8], uint32_t (&c)[8], uint32_t (&d)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
-                 "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]),
                  "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
-                 "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15])
+                 "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]),
+                 "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7])
                :
                : "memory");
 }
@@ -193,128 +213,257 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[16], uint32_t (&b)[16
 __device__ __forceinline__ float fmax4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   return fmaxf(fmaxf(__uint_as_float(a), __uint_as_float(b)), fmaxf(__uint_as_float(c), __uint_as_float(d)));
 }
+__device__ __forceinline__ uint32_t pack_relu_bias(float x, float y, const float* b) {
+  return pack_bf16(relu(x + b[0]), relu(y + b[1]));
+}
 
-// conv1 epilogue of tile t of region s: lane l of warp w holds window
-// (v, u) = (8 t + 2 w + l / 16, l % 16); its 4 x 16 columns are the window's
-// pixels; the pooled pixel (16 channels) goes to padded (v + 1, u + 1).
+// The two warps w and w + 4 read the same tensor-memory lanes (lane quadrant
+// w % 4) and split the channels: warp half h = w / 4 takes the upper or lower
+// half of them.
+
+// conv1 epilogue of tile t of region s: lane l of quadrant wq holds window
+// (v, u) = (8 t + 2 wq + l / 16, l % 16); its 4 x 16 columns are the window's
+// pixels; the pooled channels 8 h .. 8 h + 7 go to plane h at padded
+// (v + 1, u + 1).
 __device__ __forceinline__ void conv1_epilogue(uint32_t taddr, unsigned char* act1, int s, int t, const float* cb,
                                                int warp, int lane) {
-  uint32_t r0[16], r1[16], r2[16], r3[16];
-  tmem_ld16_nw(taddr, r0);
-  tmem_ld16_nw(taddr + 16, r1);
-  tmem_ld16_nw(taddr + 32, r2);
-  tmem_ld16_nw(taddr + 48, r3);
-  tmem_wait_ld(r0, r1);
-  tmem_wait_ld(r2, r3);
-  uint32_t w[8];
+  const int h = warp >> 2, wq = warp & 3;
+  uint32_t r0[8], r1[8], r2[8], r3[8];
+  tmem_ld8_nw(taddr + 8 * h, r0);
+  tmem_ld8_nw(taddr + 16 + 8 * h, r1);
+  tmem_ld8_nw(taddr + 32 + 8 * h, r2);
+  tmem_ld8_nw(taddr + 48 + 8 * h, r3);
+  tmem_wait_ld(r0, r1, r2, r3);
+  const float* b = cb + 8 * h;
+  uint32_t w[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
-    w[i] = pack_bf16(relu(fmax4(r0[2 * i], r1[2 * i], r2[2 * i], r3[2 * i]) + cb[2 * i]),
-                     relu(fmax4(r0[2 * i + 1], r1[2 * i + 1], r2[2 * i + 1], r3[2 * i + 1]) + cb[2 * i + 1]));
-  const int v = 8 * t + 2 * warp + (lane >> 4), u = lane & 15;
-  unsigned char* p = act1 + a1_off(s, 0, v + 1, u + 1);
-  *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
-  *reinterpret_cast<uint4*>(p + kA1Plane) = make_uint4(w[4], w[5], w[6], w[7]);
+  for (int i = 0; i < 4; ++i)
+    w[i] = pack_relu_bias(fmax4(r0[2 * i], r1[2 * i], r2[2 * i], r3[2 * i]),
+                          fmax4(r0[2 * i + 1], r1[2 * i + 1], r2[2 * i + 1], r3[2 * i + 1]), b + 2 * i);
+  const int v = 8 * t + 2 * wq + (lane >> 4), u = lane & 15;
+  *reinterpret_cast<uint4*>(act1 + a1_off(s, h, v + 1, u + 1)) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// conv2 epilogue of the pair: lane l of warp w is M row 32 w + l = 8 i + u,
-// i = 2 v + s: window (v, u) of region s; column group g = window pixel.  The
-// pooled pixel (32 channels) goes to row v + 1, column 10 s + u + 1 of the
-// stacked conv3 map, 8 channels per plane.
+// conv2 epilogue of the pair: lane l of quadrant wq is M row 32 wq + l =
+// 8 i + u, i = 2 v + s: window (v, u) of region s; column group g (32 columns)
+// = window pixel.  The pooled channels 16 h .. 16 h + 15 go to planes 2 h and
+// 2 h + 1 at row v + 1, column 10 s + u + 1 of the stacked conv3 map.
 __device__ __forceinline__ void conv2_epilogue(uint32_t taddr, unsigned char* act2, const float* cb, int warp,
                                                int lane) {
-  float m[32];
-  {
-    uint32_t a0[16], a1[16], b0[16], b1[16];
-    tmem_ld16_nw(taddr, a0);
-    tmem_ld16_nw(taddr + 16, a1);
-    tmem_ld16_nw(taddr + 32, b0);
-    tmem_ld16_nw(taddr + 48, b1);
-    tmem_wait_ld(a0, a1);
-    tmem_wait_ld(b0, b1);
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      m[c] = fmaxf(__uint_as_float(a0[c]), __uint_as_float(b0[c]));
-      m[16 + c] = fmaxf(__uint_as_float(a1[c]), __uint_as_float(b1[c]));
-    }
-  }
-  {
-    uint32_t a0[16], a1[16], b0[16], b1[16];
-    tmem_ld16_nw(taddr + 64, a0);
-    tmem_ld16_nw(taddr + 80, a1);
-    tmem_ld16_nw(taddr + 96, b0);
-    tmem_ld16_nw(taddr + 112, b1);
-    tmem_wait_ld(a0, a1);
-    tmem_wait_ld(b0, b1);
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      m[c] = fmaxf(m[c], fmaxf(__uint_as_float(a0[c]), __uint_as_float(b0[c])));
-      m[16 + c] = fmaxf(m[16 + c], fmaxf(__uint_as_float(a1[c]), __uint_as_float(b1[c])));
-    }
-  }
-  const int i = 4 * warp + (lane >> 3), v = i >> 1, s = i & 1, u = lane & 7;
-  const float* b = cb + 16;
+  const int h = warp >> 2, wq = warp & 3;
+  const int i = 4 * wq + (lane >> 3), v = i >> 1, s = i & 1, u = lane & 7;
   unsigned char* p = act2 + ((v + 1) * 20 + 10 * s + u + 1) * 16;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int c = 8 * q;
-    *reinterpret_cast<uint4*>(p + q * kA3Plane) =
-        make_uint4(pack_bf16(relu(m[c] + b[c]), relu(m[c + 1] + b[c + 1])),
-                   pack_bf16(relu(m[c + 2] + b[c + 2]), relu(m[c + 3] + b[c + 3])),
-                   pack_bf16(relu(m[c + 4] + b[c + 4]), relu(m[c + 5] + b[c + 5])),
-                   pack_bf16(relu(m[c + 6] + b[c + 6]), relu(m[c + 7] + b[c + 7])));
+  for (int e = 0; e < 2; ++e) {
+    const int c0 = 16 * h + 8 * e;
+    uint32_t r0[8], r1[8], r2[8], r3[8];
+    tmem_ld8_nw(taddr + c0, r0);
+    tmem_ld8_nw(taddr + 32 + c0, r1);
+    tmem_ld8_nw(taddr + 64 + c0, r2);
+    tmem_ld8_nw(taddr + 96 + c0, r3);
+    tmem_wait_ld(r0, r1, r2, r3);
+    const float* b = cb + 16 + c0;
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = pack_relu_bias(fmax4(r0[2 * k], r1[2 * k], r2[2 * k], r3[2 * k]),
+                            fmax4(r0[2 * k + 1], r1[2 * k + 1], r2[2 * k + 1], r3[2 * k + 1]), b + 2 * k);
+    *reinterpret_cast<uint4*>(p + (2 * h + e) * kA3Plane) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
-// conv3 epilogue of a pair: lane l of warp w holds core matrix k = 4w + l / 8
-// (region s = k & 1, output row i = k >> 1), column l % 8; the y neighbour is
-// 16 lanes away.  Butterfly pool: partners (lane ^ 1, then lane ^ 16) trade
-// halves of their channels and keep the maximum, so each lane of a window ends
-// with channels 8 q .. 8 q + 7, q = 2 (lane & 1) + (lane >> 4 & 1).  Pooled
-// pixel (py = w, px) of region s goes to the region's feature row at
-// (py * 4 + px) * 32 + 8 q.
+// conv3 epilogue of a pair (three partial sums, 32 columns apart): lane l of
+// quadrant wq holds core matrix k = 4 wq + l / 8 (region s = k & 1, output row i = k >> 1), column l % 8; the
+// y neighbour is 16 lanes away.  Butterfly pool over the warp's 16 channels
+// 16 h ..: partners (lane ^ 1, then lane ^ 16) trade halves and keep the
+// maximum, so each lane of a window ends with channels 16 h + 4 q .. + 3,
+// q = 2 (lane & 1) + (lane >> 4 & 1).  Pooled pixel (py = wq, px) of region s
+// goes to the region's feature row at (py * 4 + px) * 32 + 16 h + 4 q.
 __device__ __forceinline__ void conv3_epilogue(uint32_t taddr, unsigned char* feat_pair, const float* cb, int warp,
                                                int lane) {
-  uint32_t lo[16], hi[16];
-  tmem_ld16_nw(taddr, lo);
-  tmem_ld16_nw(taddr + 16, hi);
-  tmem_wait_ld(lo, hi);
+  const int h = warp >> 2, wq = warp & 3;
+  uint32_t lo0[8], hi0[8], lo1[8], hi1[8], lo2[8], hi2[8];
+  tmem_ld8_nw(taddr + 16 * h, lo0);
+  tmem_ld8_nw(taddr + 16 * h + 8, hi0);
+  tmem_ld8_nw(taddr + 32 + 16 * h, lo1);
+  tmem_ld8_nw(taddr + 32 + 16 * h + 8, hi1);
+  tmem_ld8_nw(taddr + 64 + 16 * h, lo2);
+  tmem_ld8_nw(taddr + 64 + 16 * h + 8, hi2);
+  tmem_wait_ld(lo0, hi0, lo1, hi1);
+  tmem_wait_ld(lo2, hi2, lo0, hi0);        // all loads are complete; ties the last two
   const bool xo = lane & 1, yo = (lane & 16) != 0;
-  float v[16];
+  float v[8];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const float a = __uint_as_float(lo[c]), b = __uint_as_float(hi[c]);
+  for (int c = 0; c < 8; ++c) {
+    const float a = (__uint_as_float(lo0[c]) + __uint_as_float(lo1[c])) + __uint_as_float(lo2[c]);
+    const float b = (__uint_as_float(hi0[c]) + __uint_as_float(hi1[c])) + __uint_as_float(hi2[c]);
     v[c] = fmaxf(xo ? b : a, __shfl_xor_sync(0xffffffffu, xo ? a : b, 1));
   }
 #pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = fmaxf(yo ? v[8 + c] : v[c], __shfl_xor_sync(0xffffffffu, yo ? v[c] : v[8 + c], 16));
+  for (int c = 0; c < 4; ++c) v[c] = fmaxf(yo ? v[4 + c] : v[c], __shfl_xor_sync(0xffffffffu, yo ? v[c] : v[4 + c], 16));
   const int q = 2 * (lane & 1) + ((lane >> 4) & 1);
-  const int s = (lane >> 3) & 1, px = (lane & 7) >> 1, py = warp;
-  const float* b = cb + 48 + 8 * q;
-  *reinterpret_cast<uint4*>(feat_pair + s * kFeatPitch * 2 + ((py * 4 + px) * 32 + 8 * q) * 2) =
-      make_uint4(pack_bf16(relu(v[0] + b[0]), relu(v[1] + b[1])), pack_bf16(relu(v[2] + b[2]), relu(v[3] + b[3])),
-                 pack_bf16(relu(v[4] + b[4]), relu(v[5] + b[5])), pack_bf16(relu(v[6] + b[6]), relu(v[7] + b[7])));
+  const int s = (lane >> 3) & 1, px = (lane & 7) >> 1, py = wq;
+  const float* b = cb + 48 + 16 * h + 4 * q;
+  *reinterpret_cast<uint2*>(feat_pair + s * kFeatPitch * 2 + ((py * 4 + px) * 32 + 16 * h + 4 * q) * 2) =
+      make_uint2(pack_relu_bias(v[0], v[1], b), pack_relu_bias(v[2], v[3], b + 2));
 }
 
-// the region that CTA position `idx` (0 .. kGroupT) of the group at `base`
-// computes; the position kGroupT is the next group's first.  A region past
-// the end is clamped: computed, never written out.
-__device__ __forceinline__ long long infer_region(const InferArgs& a, long long base, long long stride, int idx) {
-  const long long r = idx < kGroupT ? base + idx : base + stride + (idx - kGroupT);
+// Region s (0, 1) of pair k of this CTA: pairs run through the CTA's groups
+// of 16 regions (group n at blockIdx.x * 16 + n * stride), 8 pairs a group.
+// A region past the end is clamped: computed, never written out.
+__device__ __forceinline__ long long pair_region(const InferArgs& a, long long k, int s) {
+  const long long n = k / kPairsT;
+  const long long r = (static_cast<long long>(blockIdx.x) + n * gridDim.x) * kGroupT + 2 * (k - n * kPairsT) + s;
   return r < a.n_regions ? r : a.n_regions - 1;
 }
 
-template <typename InT>
-__global__ void __launch_bounds__(kThreadsT, 2) cnn_infer_tc_kernel(const InferArgs a, int* __restrict__ err,
-                                                                     long long wait_limit) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar1[4];   // conv1 tiles (region, tile) of the pair
-  __shared__ __align__(8) uint64_t bar2;      // conv2 of the pair
-  __shared__ __align__(8) uint64_t bar3;      // conv3 of the pair
-  __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
+// barrier among the epilogue warps only (hardware barrier 1)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreadsT) : "memory"); }
+// the same, returning whether `pred` holds in every epilogue thread
+__device__ __forceinline__ bool epi_sync_and(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(pred)), "n"(kThreadsT)
+      : "memory");
+  return r != 0;
+}
+
+// Wait for phase `parity` of `bar`; false once the CTA has given up (the
+// shared flag `abort`) or after about `limit` SM cycles, which also sets the flag.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, long long limit, volatile int* abort) {
+  if (mbar_try_wait(bar, parity, 2000u)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity, 2000u)) {
+    if (*abort) return false;
+    if (clock64() - t0 > limit) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// FC1 and the per-slot head of the group at `base` (epilogue warps; features complete)
+//   u = Wf1 f (FC1; warp (mt, kh) = neuron tile of 16 x half of K, both region tiles, so that each
+//       Wf1 fragment is read once; the two K halves are added in a fixed order)
+//   g = bf16(relu(u + fb1 + Wq[:, slot]))  per (region, slot): rows region * 4 + slot
+//   logits = g Wf2^T + fb2  (warp-level MMA: 4 row tiles x 3 label tiles of 8, K = 64)
+//   label = the first maximum, margin = best minus second best
+__device__ __forceinline__ void group_head(const InferArgs& a, long long base, unsigned char* sm, int tid) {
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const unsigned char* feat = sm + kTFeat;
+  float* u_s = reinterpret_cast<float*>(sm + kTU);
+  uint16_t* g_s = reinterpret_cast<uint16_t*>(sm + kTG);
+  float* logit_s = reinterpret_cast<float*>(sm + kTLogit);
+  const float* fb1 = reinterpret_cast<const float*>(sm + kTHead);
+  const float* wq = fb1 + kHidden;
+  const float* fb2 = wq + kHidden * kSlots + kLabels * kF2Pitch;
+  const int ns = a.n_slots;
   {
+    const int mt = warp & 3, kh = warp >> 2;
+    const uint4* f1 = reinterpret_cast<const uint4*>(a.packed + kPkF1) + mt * 32 * 32 + lane;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    const uint32_t b_lane = smem_u32(feat) + ((lane & 7) * kFeatPitch + (lane >> 3) * 8) * 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int ks = 16 * kh + 2 * i;
+      const uint4 a0 = __ldg(f1 + ks * 32), a1 = __ldg(f1 + (ks + 1) * 32);
+      const uint32_t af0[4] = {a0.x, a0.y, a0.z, a0.w}, af1[4] = {a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        uint32_t bb[4];
+        ldsm_x4(bb, b_lane + nt * 8 * kFeatPitch * 2 + ks * 32);
+        const uint32_t b0[2] = {bb[0], bb[1]}, b1[2] = {bb[2], bb[3]};
+        mma_bf16(acc[nt], af0, b0);
+        mma_bf16(acc[nt], af1, b1);
+      }
+    }
+    float* up = u_s + kh * kGroupT * kHidden;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int n0 = mt * 16 + g, r0 = nt * 8 + 2 * t;
+      up[r0 * kHidden + n0] = acc[nt][0];
+      up[(r0 + 1) * kHidden + n0] = acc[nt][1];
+      up[r0 * kHidden + n0 + 8] = acc[nt][2];
+      up[(r0 + 1) * kHidden + n0 + 8] = acc[nt][3];
+    }
+  }
+  epi_sync();
+  for (int i = tid; i < kGroupT * kHidden; i += kThreadsT) {
+    const int h = i % kHidden, region = i / kHidden;
+    const float uh = (u_s[i] + u_s[kGroupT * kHidden + i]) + fb1[h];
+#pragma unroll
+    for (int si = 0; si < kSlots; ++si)
+      if (si < ns) g_s[(region * kSlots + si) * kHPitch + h] = static_cast<uint16_t>(bf16_bits(relu(uh + wq[h * kSlots + a.slots[si]])));
+  }
+  epi_sync();
+  {
+    const int mt = warp & 3;
+    const uint32_t a_lane = smem_u32(g_s) + ((mt * 16 + (lane & 15)) * kHPitch + (lane >> 4) * 8) * 2;
+    for (int nt = warp >> 2; nt < 3; nt += 2) {
+      const uint32_t b_lane = smem_u32(sm + kTW2) + ((nt * 8 + (lane & 7)) * kHPitch + (lane >> 3) * 8) * 2;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kk = 0; kk < 4; kk += 2) {
+        uint32_t a0[4], a1[4], bb[4];
+        ldsm_x4(a0, a_lane + kk * 32);
+        ldsm_x4(a1, a_lane + (kk + 1) * 32);
+        ldsm_x4(bb, b_lane + kk * 32);
+        const uint32_t b0[2] = {bb[0], bb[1]}, b1[2] = {bb[2], bb[3]};
+        mma_bf16(acc, a0, b0);
+        mma_bf16(acc, a1, b1);
+      }
+      const int r0 = mt * 16 + g, j0 = nt * 8 + 2 * t;
+      if (j0 < kLabels) {
+        logit_s[r0 * kLabels + j0] = acc[0] + fb2[j0];
+        logit_s[(r0 + 8) * kLabels + j0] = acc[2] + fb2[j0];
+      }
+      if (j0 + 1 < kLabels) {
+        logit_s[r0 * kLabels + j0 + 1] = acc[1] + fb2[j0 + 1];
+        logit_s[(r0 + 8) * kLabels + j0 + 1] = acc[3] + fb2[j0 + 1];
+      }
+    }
+  }
+  epi_sync();
+  if (tid < kGroupT * ns) {
+    const int region = tid / ns, si = tid - region * ns;
+    const long long reg = base + region;
+    if (reg < a.n_regions) {
+      const float* l = logit_s + (region * kSlots + si) * kLabels;
+      int best = 0;
+      float b1 = l[0], b2 = -INFINITY;
+      for (int j = 1; j < kLabels; ++j) {
+        if (l[j] > b1) { b2 = b1; b1 = l[j]; best = j; }
+        else if (l[j] > b2) b2 = l[j];
+      }
+      const long long o = static_cast<long long>(si) * a.n_regions + reg;
+      a.labels[o] = static_cast<unsigned char>(best);
+      if (a.margin != nullptr) a.margin[o] = b1 - b2;
+      if (a.logits != nullptr)
+        for (int j = 0; j < kLabels; ++j) a.logits[o * kLabels + j] = l[j];
+    }
+  }
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(kBlockT, 1) cnn_infer_tc_kernel(const InferArgs a, int* __restrict__ err,
+                                                                   long long wait_limit) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar1[4];     // conv1 tile (region, tile) of a pair done
+  __shared__ __align__(8) uint64_t bar2, bar3;  // conv2 / conv3 of a pair done
+  __shared__ __align__(8) uint64_t e_full[2], e_empty[2];   // expanded-map slots staged / read
+  __shared__ __align__(8) uint64_t c1_done, c2_done, c3_done;   // epilogues done (accumulators free, maps written)
+  __shared__ __align__(8) uint64_t bar_fin;     // every MMA of the CTA done
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < kThreadsT) {
     const float* cbs = reinterpret_cast<const float*>(a.packed + kPkCB);
     for (int i = tid; i < 80; i += kThreadsT) reinterpret_cast<float*>(sm + kTCB)[i] = cbs[i];
     const float* hs = reinterpret_cast<const float*>(a.packed + kPkHead);
@@ -323,8 +472,13 @@ __global__ void __launch_bounds__(kThreadsT, 2) cnn_infer_tc_kernel(const InferA
     for (int i = tid; i < nq; i += kThreadsT) hd[i] = hs[i];
     for (int i = tid; i < kLabels * kHidden; i += kThreadsT) hd[nq + (i / kHidden) * kF2Pitch + i % kHidden] = hs[nq + i];
     for (int i = tid; i < kLabels; i += kThreadsT) hd[nq + kLabels * kF2Pitch + i] = hs[nq + kLabels * kHidden + i];
+    for (int i = tid; i < 24 * kHPitch; i += kThreadsT) {
+      const int j = i / kHPitch, h = i % kHPitch;
+      reinterpret_cast<uint16_t*>(sm + kTW2)[i] =
+          (j < kLabels && h < kHidden) ? static_cast<uint16_t>(bf16_bits(hs[nq + j * kHidden + h])) : static_cast<uint16_t>(0);
+    }
     pack_b_operands(a.packed, sm, tid);
-    // zero both activation maps (borders stay zero; interiors are rewritten)
+    // zero the activation maps (borders stay zero; interiors are rewritten)
     for (int i = tid; i < (kTFeat - kTAct1) / 16; i += kThreadsT)
       reinterpret_cast<uint4*>(sm + kTAct1)[i] = make_uint4(0, 0, 0, 0);
   }
@@ -333,6 +487,15 @@ __global__ void __launch_bounds__(kThreadsT, 2) cnn_infer_tc_kernel(const InferA
     for (int j = 0; j < 4; ++j) mbar_init(&bar1[j], 1);
     mbar_init(&bar2, 1);
     mbar_init(&bar3, 1);
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&e_full[j], kProducerWarps);
+      mbar_init(&e_empty[j], 1);
+    }
+    mbar_init(&c1_done, kWarpsT);
+    mbar_init(&c2_done, kWarpsT);
+    mbar_init(&c3_done, kWarpsT);
+    mbar_init(&bar_fin, 1);
+    abort_flag = 0;
     fence_mbar_init();
   }
   fence_proxy_async_smem();                   // B operands and zeroed maps are read by the tensor cores
@@ -340,187 +503,142 @@ __global__ void __launch_bounds__(kThreadsT, 2) cnn_infer_tc_kernel(const InferA
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
+  const long long n_groups = (a.n_regions + kGroupT - 1) / kGroupT;
+  const long long pairs = (n_groups - blockIdx.x + gridDim.x - 1) / gridDim.x * kPairsT;
 
-  const float* cb = reinterpret_cast<const float*>(sm + kTCB);
-  unsigned char* feat = sm + kTFeat;
-  unsigned char* act1 = sm + kTAct1;
-  unsigned char* act2 = sm + kTAct2;
-  float* u_s = reinterpret_cast<float*>(sm + kTU);
-  float* logit_s = reinterpret_cast<float*>(sm + kTLogit);
-  float* g_s = reinterpret_cast<float*>(sm + kTAct1);       // the head's hidden values (the map is free then)
-  const float* fb1 = reinterpret_cast<const float*>(sm + kTHead);
-  const float* wq = fb1 + kHidden;
-  const float* wf2 = wq + kHidden * kSlots;
-  const float* fb2 = wf2 + kLabels * kF2Pitch;
-  const int ns = a.n_slots;
-  constexpr uint32_t idesc64 = idesc_bf16_f32(128, 64), idesc32 = idesc_bf16_f32(128, 32);
-  const uint32_t e_s = smem_u32(sm + kTE), act1_s = smem_u32(act1), act2_s = smem_u32(act2);
-  const uint32_t b1_s = smem_u32(sm + kTB1), b2_s = smem_u32(sm + kTB2), b3_s = smem_u32(sm + kTB3);
-  const uint32_t wl = static_cast<uint32_t>(warp * 32) << 16;   // the warp's tensor-memory lanes
-  const long long stride = static_cast<long long>(gridDim.x) * kGroupT;
-  uint32_t ph = 0;
-  bool ok = true, failed = false;
-  int px0[10], px1[10];
-  {
-    const long long base0 = static_cast<long long>(blockIdx.x) * kGroupT;
-    load_region_rows<InT>(a, infer_region(a, base0, stride, 0), warp, lane, px0);
-    load_region_rows<InT>(a, infer_region(a, base0, stride, 1), warp, lane, px1);
-  }
-
-  for (long long base = static_cast<long long>(blockIdx.x) * kGroupT; base < a.n_regions && !failed; base += stride) {
-#pragma unroll 1
-    for (int pr = 0; pr < kGroupT / 2 && !failed; ++pr) {
-      store_expanded(px0, sm + kTE, warp, lane);
-      store_expanded(px1, sm + kTE + kEBytes, warp, lane);
-      fence_proxy_async_smem();               // the expanded maps are read by the tensor cores
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      // conv1: tile (s, t) = window rows 8 t .. 8 t + 7 of region s, one MMA of K = 16, N = 64
-      if (tid == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int s = q >> 1, tt = q & 1;
-          umma_bf16(tmem + (s ? kC1Col1 : kC1Col0) + 64 * tt,
-                    umma_desc(e_s + s * kEBytes + tt * 8 * kERow, kERow, 128), umma_desc(b1_s, 128, 256), idesc64, 0u);
-          umma_commit(&bar1[q]);
-        }
-      }
-      load_region_rows<InT>(a, infer_region(a, base, stride, 2 * pr + 2), warp, lane, px0);
-      load_region_rows<InT>(a, infer_region(a, base, stride, 2 * pr + 3), warp, lane, px1);
-#pragma unroll 1
-      for (int q = 0; q < 4; ++q) {
-        ok &= mbar_wait_bounded(&bar1[q], ph, wait_limit);
+  if (warp >= kProducerWarp0) {
+    // staging: expanded maps of pair k into slot k % 2, once conv1 of pair k - 2 has read it;
+    // warp p does half p % 2 of region p / 2
+    const int pw = warp - kProducerWarp0, rs = pw >> 1, half = pw & 1;
+    int px[kStageRows];
+    load_half_region<InT>(a, pair_region(a, 0, rs), half, lane, px);
+    for (long long k = 0; k < pairs; ++k) {
+      const int slot = static_cast<int>(k & 1);
+      if (k >= 2 && !wait_or_abort(&e_empty[slot], static_cast<uint32_t>(((k - 2) >> 1) & 1), wait_limit, abort)) break;
+      store_half_expanded(px, half, sm + kTE + (2 * slot + rs) * kEBytes, lane);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&e_full[slot]);
+      if (k + 1 < pairs) load_half_region<InT>(a, pair_region(a, k + 1, rs), half, lane, px);
+    }
+  } else if (warp == kIssuerWarp) {
+    // MMA issue: iteration k issues conv1 of pair k, conv2 of pair k - 1, conv3 of pair k - 2
+    const uint32_t e_s = smem_u32(sm + kTE), act1_s = smem_u32(sm + kTAct1), act2_s = smem_u32(sm + kTAct2);
+    const uint32_t b1_s = smem_u32(sm + kTB1), b2_s = smem_u32(sm + kTB2), b3_s = smem_u32(sm + kTB3);
+    constexpr uint32_t idesc64 = idesc_bf16_f32(128, 64), idesc128 = idesc_bf16_f32(128, 128);
+    constexpr uint32_t idesc32 = idesc_bf16_f32(128, 32);
+    for (long long k = 0; k < pairs + 2; ++k) {
+      if (k < pairs) {
+        const int slot = static_cast<int>(k & 1);
+        if (!wait_or_abort(&e_full[slot], static_cast<uint32_t>((k >> 1) & 1), wait_limit, abort)) break;
+        if (k >= 1 && !wait_or_abort(&c1_done, static_cast<uint32_t>((k - 1) & 1), wait_limit, abort)) break;
         tc_fence_after();
-        const int s = q >> 1, tt = q & 1;
-        conv1_epilogue(tmem + wl + (s ? kC1Col1 : kC1Col0) + 64 * tt, act1, s, tt, cb, warp, lane);
-      }
-      fence_proxy_async_smem();               // the conv2 input map is read by the tensor cores
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      // conv2 of the pair: window pixel gp = (py, px) x tap (dy, dx), K = 16 over 2 planes, N = 32
-      if (tid == 0) {
+        if (lane == 0) {
+          // conv1 tile q = (region s, window rows 8 t ..): one MMA of K = 16, N = 64
 #pragma unroll
-        for (int gp = 0; gp < 4; ++gp) {
-#pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            const int ry = (gp >> 1) + tap / 3, rx = (gp & 1) + tap % 3;
-            const uint32_t ab = act1_s + (ry & 1) * kRPar + (ry >> 1) * kRP + (rx & 1) * kCPar + (rx >> 1) * 16;
-            umma_bf16(tmem + kC2Col + 32 * gp, umma_desc(ab, kA1Plane, kRS), umma_desc(b2_s + tap * 1024, 128, 256),
-                      idesc32, tap > 0 ? 1u : 0u);
+          for (int q = 0; q < 4; ++q) {
+            umma_bf16(tmem + kC1Col + 64 * q,
+                      umma_desc(e_s + (2 * slot + (q >> 1)) * kEBytes + (q & 1) * 8 * kERow, kERow, 128),
+                      umma_desc(b1_s, 128, 256), idesc64, 0u);
+            umma_commit(&bar1[q]);
           }
+          umma_commit(&e_empty[slot]);
         }
-        umma_commit(&bar2);
+        __syncwarp();
+      } else if (k == pairs) {
+        if (!wait_or_abort(&c1_done, static_cast<uint32_t>((k - 1) & 1), wait_limit, abort)) break;
+        tc_fence_after();
       }
-      ok &= mbar_wait_bounded(&bar2, ph, wait_limit);
-      tc_fence_after();
-      conv2_epilogue(tmem + wl + kC2Col, act2, cb, warp, lane);
-      fence_proxy_async_smem();               // the stacked conv3 map is read by the tensor cores
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      // conv3 of the pair: 9 taps x 2 channel halves of K = 16, N = 32
-      if (tid == 0) {
+      if (k >= 1 && k <= pairs) {
+        if (k >= 2 && !wait_or_abort(&c2_done, static_cast<uint32_t>((k - 2) & 1), wait_limit, abort)) break;
+        tc_fence_after();
+        if (lane == 0) {
+          // conv2 of pair k - 1: receptive-field offset (ry, rx) of the windows, K = 16 over 2 planes,
+          // N = 128 (window pixel x channel; zero weights where the offset is not a tap of that pixel)
+          const uint32_t m1 = act1_s + static_cast<uint32_t>((k - 1) & 1) * kAct1T;
 #pragma unroll
-        for (int k = 0; k < 18; ++k) {
-          const int tap = k >> 1, h = k & 1;
-          umma_bf16(tmem + kC3Col, umma_desc(act2_s + ((tap / 3) * 20 + tap % 3) * 16 + 2 * h * kA3Plane, kA3Plane, 160),
-                    umma_desc(b3_s + k * 1024, 128, 256), idesc32, k > 0 ? 1u : 0u);
+          for (int off = 0; off < 16; ++off) {
+            const int ry = off >> 2, rx = off & 3;
+            const uint32_t ab = m1 + (ry & 1) * kRPar + (ry >> 1) * kRP + (rx & 1) * kCPar + (rx >> 1) * 16;
+            umma_bf16(tmem + kC2Col, umma_desc(ab, kA1Plane, kRS), umma_desc(b2_s + off * 4096, 128, 256), idesc128,
+                      off > 0 ? 1u : 0u);
+          }
+          umma_commit(&bar2);
         }
-        umma_commit(&bar3);
+        __syncwarp();
+      } else if (k == pairs + 1) {
+        if (!wait_or_abort(&c2_done, static_cast<uint32_t>((k - 2) & 1), wait_limit, abort)) break;
+        tc_fence_after();
       }
-      ok &= mbar_wait_bounded(&bar3, ph, wait_limit);
-      tc_fence_after();
-      conv3_epilogue(tmem + wl + kC3Col, feat + (2 * pr) * kFeatPitch * 2, cb, warp, lane);
-      ph ^= 1u;
-      tc_fence_before();
-      failed = !__syncthreads_and(ok);        // features written; tensor memory and maps free again
-      tc_fence_after();
-    }
-    if (failed) break;
-    // FC1: u[16 regions][64] = features x Wf1^T (warp-level MMA); warp = neuron tile of 16
-    {
-      const int mt = warp;
-      const uint4* f1 = reinterpret_cast<const uint4*>(a.packed + kPkF1) + mt * 32 * 32 + lane;
+      if (k >= 2) {
+        if (k >= 3 && !wait_or_abort(&c3_done, static_cast<uint32_t>((k - 3) & 1), wait_limit, abort)) break;
+        tc_fence_after();
+        if (lane == 0) {
+          // conv3 of pair k - 2: 9 taps x 2 channel halves of K = 16, N = 32, K-step j into partial sum j % 3
+          const uint32_t m2 = act2_s + static_cast<uint32_t>(k & 1) * kAct2T;
 #pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        const uint32_t b_lane = smem_u32(feat) + ((nt * 8 + (lane & 7)) * kFeatPitch + (lane >> 3) * 8) * 2;
-#pragma unroll 4
-        for (int ks = 0; ks < 32; ks += 2) {
-          uint32_t bb[4];
-          ldsm_x4(bb, b_lane + ks * 32);
-          const uint4 a0 = __ldg(f1 + ks * 32), a1 = __ldg(f1 + (ks + 1) * 32);
-          const uint32_t af0[4] = {a0.x, a0.y, a0.z, a0.w}, af1[4] = {a1.x, a1.y, a1.z, a1.w};
-          const uint32_t b0[2] = {bb[0], bb[1]}, b1[2] = {bb[2], bb[3]};
-          mma_bf16(acc, af0, b0);
-          mma_bf16(acc, af1, b1);
+          for (int j = 0; j < 18; ++j) {
+            const int tap = j >> 1, h = j & 1;
+            umma_bf16(tmem + kC3Col + 32 * (j % 3),
+                      umma_desc(m2 + ((tap / 3) * 20 + tap % 3) * 16 + 2 * h * kA3Plane, kA3Plane, 160),
+                      umma_desc(b3_s + j * 1024, 128, 256), idesc32, j >= 3 ? 1u : 0u);
+          }
+          umma_commit(&bar3);
         }
-        const int n0 = mt * 16 + g, r0 = nt * 8 + 2 * t;
-        u_s[r0 * kHidden + n0] = acc[0];
-        u_s[(r0 + 1) * kHidden + n0] = acc[1];
-        u_s[r0 * kHidden + n0 + 8] = acc[2];
-        u_s[(r0 + 1) * kHidden + n0 + 8] = acc[3];
+        __syncwarp();
       }
     }
-    __syncthreads();
-    // head, once per (region, slot): g = bf16(relu(u + fb1 + Wq[:, slot])); then
-    // logits[region][slot][label] = fb2 + Wf2 g
-    for (int i = tid; i < kGroupT * ns * kHidden; i += kThreadsT) {
-      const int h = i % kHidden, rs = i / kHidden, si = rs % ns, region = rs / ns;
-      g_s[(region * kSlots + si) * kHidden + h] =
-          round_bf16(relu((u_s[region * kHidden + h] + fb1[h]) + wq[h * kSlots + a.slots[si]]));
-    }
-    __syncthreads();
-    {
-      const int per = ns * kLabels;
-      for (int task = tid; task < kGroupT * per; task += kThreadsT) {
-        const int region = task / per, rem = task - region * per;
-        const int si = rem / kLabels, j = rem - si * kLabels;
-        const float* gv = g_s + (region * kSlots + si) * kHidden;
-        const float* w = wf2 + j * kF2Pitch;
-        float acc = fb2[j];
-#pragma unroll 8
-        for (int h = 0; h < kHidden; ++h) acc = fmaf(w[h], gv[h], acc);
-        logit_s[(region * kSlots + si) * kLabels + j] = acc;
-      }
-    }
-    __syncthreads();
-    if (tid < kGroupT * ns) {
-      const int region = tid / ns, si = tid - region * ns;
-      const long long reg = base + region;
-      if (reg < a.n_regions) {
-        const float* l = logit_s + (region * kSlots + si) * kLabels;
-        int best = 0;
-        float b1 = l[0], b2 = -INFINITY;
-        for (int j = 1; j < kLabels; ++j) {
-          if (l[j] > b1) { b2 = b1; b1 = l[j]; best = j; }
-          else if (l[j] > b2) b2 = l[j];
+    // every MMA this thread issued has finished before the tensor memory is freed
+    if (lane == 0) umma_commit(&bar_fin);
+    __syncwarp();
+    if (!mbar_wait_bounded(&bar_fin, 0u, wait_limit)) *abort = 1;
+  } else {
+    // epilogue warps
+    const float* cb = reinterpret_cast<const float*>(sm + kTCB);
+    const uint32_t wl = static_cast<uint32_t>((warp & 3) * 32) << 16;   // the warp's tensor-memory lanes
+    bool ok = true;
+    for (long long k = 0; k < pairs + 2; ++k) {
+      if (k < pairs) {
+        unsigned char* m1 = sm + kTAct1 + (k & 1) * kAct1T;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+          ok &= wait_or_abort(&bar1[q], static_cast<uint32_t>(k & 1), wait_limit, abort);
+          tc_fence_after();
+          conv1_epilogue(tmem + wl + kC1Col + 64 * q, m1, q >> 1, q & 1, cb, warp, lane);
         }
-        const long long o = static_cast<long long>(si) * a.n_regions + reg;
-        a.labels[o] = static_cast<unsigned char>(best);
-        if (a.margin != nullptr) a.margin[o] = b1 - b2;
-        if (a.logits != nullptr)
-          for (int j = 0; j < kLabels; ++j) a.logits[o * kLabels + j] = l[j];
+        fence_proxy_async_smem();             // the conv2 input map is read by the tensor cores
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c1_done);
+      }
+      if (k >= 1 && k <= pairs) {
+        ok &= wait_or_abort(&bar2, static_cast<uint32_t>((k - 1) & 1), wait_limit, abort);
+        tc_fence_after();
+        conv2_epilogue(tmem + wl + kC2Col, sm + kTAct2 + ((k - 1) & 1) * kAct2T, cb, warp, lane);
+        fence_proxy_async_smem();             // the stacked conv3 map is read by the tensor cores
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c2_done);
+      }
+      if (k >= 2) {
+        const int pr = static_cast<int>((k - 2) % kPairsT);
+        ok &= wait_or_abort(&bar3, static_cast<uint32_t>((k - 2) & 1), wait_limit, abort);
+        tc_fence_after();
+        conv3_epilogue(tmem + wl + kC3Col, sm + kTFeat + 2 * pr * kFeatPitch * 2, cb, warp, lane);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c3_done);
+        if (pr == kPairsT - 1) {              // the group of pair k - 2 is complete
+          if (!epi_sync_and(ok && *abort == 0)) break;
+          const long long n = (k - 2) / kPairsT;
+          group_head(a, (static_cast<long long>(blockIdx.x) + n * gridDim.x) * kGroupT, sm, tid);
+        }
       }
     }
-    // the head's hidden values used the conv2 input map: clear it (its borders
-    // must be zero) before the next group's first pair
-    __syncthreads();
-    for (int i = tid; i < kAct1T / 16; i += kThreadsT) reinterpret_cast<uint4*>(sm + kTAct1)[i] = make_uint4(0, 0, 0, 0);
-    fence_proxy_async_smem();
-    __syncthreads();
-  }
-  if (failed && tid == 0) {
-    atomicOr(err, 2);
-    // the MMAs that may still run: each barrier's last armed phase
-    for (int j = 0; j < 4; ++j) (void)mbar_wait_bounded(&bar1[j], ph ^ 1u, wait_limit);
-    (void)mbar_wait_bounded(&bar2, ph ^ 1u, wait_limit);
-    (void)mbar_wait_bounded(&bar3, ph ^ 1u, wait_limit);
   }
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && abort_flag) atomicOr(err, 2);
   if (warp == 0) tmem_dealloc(tmem, kTmemColsT);
 }
 
@@ -530,11 +648,10 @@ int launch_infer_tc_t(const InferArgs& a, int num_sms, int* err, void* stream) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemT);
   if (e != cudaSuccess) return static_cast<int>(e);
   const long long groups = (a.n_regions + kGroupT - 1) / kGroupT;
-  const long long cap = 2ll * num_sms;
-  const int grid = static_cast<int>(groups < cap ? groups : cap);
+  const int grid = static_cast<int>(groups < num_sms ? groups : num_sms);
   if (grid <= 0) return 0;
   long long limit = kDefaultWaitLimit;
   (void)fault_mode(&limit);
-  kern<<<grid, kThreadsT, kSmemT, static_cast<cudaStream_t>(stream)>>>(a, err, limit);
+  kern<<<grid, kBlockT, kSmemT, static_cast<cudaStream_t>(stream)>>>(a, err, limit);
   return static_cast<int>(cudaGetLastError());
 }
