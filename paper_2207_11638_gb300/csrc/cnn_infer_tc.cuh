@@ -37,8 +37,7 @@
 //     fill no tile: the pooled conv2 maps of the pair sit side by side in a
 //     [4][10][20][8] map; M = 128 covers both regions, core matrix
 //     k = 2 i + s (output row i of region s) at 160 k + (dy*20 + dx)*16:
-//     sbo = 160 B, lbo = 3200 B; 18 MMAs (taps x channel halves), N = 32,
-//     in three independent partial sums.
+//     sbo = 160 B, lbo = 3200 B; 18 MMAs (taps x channel halves), N = 32.
 //     The pool is a butterfly between lanes: partners trade halves of their
 //     channels and keep the maximum, twice.
 // Bias and ReLU follow the maximum (both commute with it); each pooled map is
@@ -48,7 +47,7 @@
 //
 // One CTA per SM (all 512 tensor-memory columns), warp-specialised, runs a
 // software pipeline over pairs of regions:
-//   4 staging warps load pair k + 1's pixels while expanding pair k into one
+//   2 staging warps load pair k + 1's pixels while expanding pair k into one
 //     of two expanded-map slots;
 //   1 MMA warp issues, in iteration k, conv1 of pair k, conv2 of pair k - 1
 //     and conv3 of pair k - 2 (activation maps double-buffered), each as soon
@@ -65,12 +64,12 @@
 
 constexpr int kWarpsT = 8;                       // epilogue warps (two per tensor-memory lane quadrant)
 constexpr int kThreadsT = 32 * kWarpsT;
-constexpr int kIssuerWarp = kWarpsT, kProducerWarp0 = kWarpsT + 1, kProducerWarps = 4;
+constexpr int kIssuerWarp = kWarpsT, kProducerWarp0 = kWarpsT + 1, kProducerWarps = 2;
 constexpr int kBlockT = kThreadsT + 32 * (1 + kProducerWarps);   // + the MMA-issuing warp and the staging warps
 constexpr int kGroupT = 16;                      // regions per FC1 batch
 constexpr int kPairsT = kGroupT / 2;
 constexpr uint32_t kTmemColsT = 512;
-// tensor-memory columns: conv1 of a pair (4 tiles of 64), conv2 of a pair, conv3 of a pair (3 partial sums)
+// tensor-memory columns: conv1 of a pair (4 tiles of 64), conv2 of a pair, conv3 of a pair
 constexpr uint32_t kC1Col = 0, kC2Col = 256, kC3Col = 384;
 constexpr int kERow = 16 * 16;                   // bytes per row of the expanded map
 constexpr int kEBytes = 17 * kERow;              // E[17][16] x 16 B
@@ -144,8 +143,8 @@ __device__ __forceinline__ void pack_b_operands(const unsigned char* packed, uns
   }
 }
 
-// Staging is split over four warps: warp p expands rows j of region p / 2's
-// expanded map with j in [0, 9) for even p, [9, 17) for odd p, from input
+// Staging: a warp per region of the pair expands rows j of its expanded map,
+// half 0 (j in [0, 9)) and half 1 (j in [9, 17)), from input
 // rows 2j - 1 and 2j (17 and 16 rows; replicated beyond the image, zero
 // outside the region) at the lane's column (replicated beyond the image).
 // The pixels are kept as raw integers and loaded one pair of regions ahead.
@@ -221,27 +220,32 @@ __device__ __forceinline__ uint32_t pack_relu_bias(float x, float y, const float
 // w % 4) and split the channels: warp half h = w / 4 takes the upper or lower
 // half of them.
 
-// conv1 epilogue of tile t of region s: lane l of quadrant wq holds window
-// (v, u) = (8 t + 2 wq + l / 16, l % 16); its 4 x 16 columns are the window's
-// pixels; the pooled channels 8 h .. 8 h + 7 go to plane h at padded
-// (v + 1, u + 1).
-__device__ __forceinline__ void conv1_epilogue(uint32_t taddr, unsigned char* act1, int s, int t, const float* cb,
-                                               int warp, int lane) {
+// conv1 epilogue of the pair (all four tiles loaded before one wait): tile
+// q = 2 s + t, lane l of quadrant wq holds window (v, u) = (8 t + 2 wq + l / 16,
+// l % 16) of region s; its 4 x 16 columns are the window's pixels; the pooled
+// channels 8 h .. 8 h + 7 go to plane h at padded (v + 1, u + 1).
+__device__ __forceinline__ void conv1_epilogue(uint32_t taddr, unsigned char* act1, const float* cb, int warp,
+                                               int lane) {
   const int h = warp >> 2, wq = warp & 3;
-  uint32_t r0[8], r1[8], r2[8], r3[8];
-  tmem_ld8_nw(taddr + 8 * h, r0);
-  tmem_ld8_nw(taddr + 16 + 8 * h, r1);
-  tmem_ld8_nw(taddr + 32 + 8 * h, r2);
-  tmem_ld8_nw(taddr + 48 + 8 * h, r3);
-  tmem_wait_ld(r0, r1, r2, r3);
-  const float* b = cb + 8 * h;
-  uint32_t w[4];
+  uint32_t r[4][4][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    w[i] = pack_relu_bias(fmax4(r0[2 * i], r1[2 * i], r2[2 * i], r3[2 * i]),
-                          fmax4(r0[2 * i + 1], r1[2 * i + 1], r2[2 * i + 1], r3[2 * i + 1]), b + 2 * i);
-  const int v = 8 * t + 2 * wq + (lane >> 4), u = lane & 15;
-  *reinterpret_cast<uint4*>(act1 + a1_off(s, h, v + 1, u + 1)) = make_uint4(w[0], w[1], w[2], w[3]);
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int gp = 0; gp < 4; ++gp) tmem_ld8_nw(taddr + 64 * q + 16 * gp + 8 * h, r[q][gp]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) tmem_wait_ld(r[q][0], r[q][1], r[q][2], r[q][3]);
+  const float* b = cb + 8 * h;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      w[i] = pack_relu_bias(fmax4(r[q][0][2 * i], r[q][1][2 * i], r[q][2][2 * i], r[q][3][2 * i]),
+                            fmax4(r[q][0][2 * i + 1], r[q][1][2 * i + 1], r[q][2][2 * i + 1], r[q][3][2 * i + 1]),
+                            b + 2 * i);
+    const int v = 8 * (q & 1) + 2 * wq + (lane >> 4), u = lane & 15;
+    *reinterpret_cast<uint4*>(act1 + a1_off(q >> 1, h, v + 1, u + 1)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
 }
 
 // conv2 epilogue of the pair: lane l of quadrant wq is M row 32 wq + l =
@@ -272,8 +276,7 @@ __device__ __forceinline__ void conv2_epilogue(uint32_t taddr, unsigned char* ac
   }
 }
 
-// conv3 epilogue of a pair (three partial sums, 32 columns apart): lane l of
-// quadrant wq holds core matrix k = 4 wq + l / 8 (region s = k & 1, output row i = k >> 1), column l % 8; the
+// conv3 epilogue of a pair: lane l of quadrant wq holds core matrix k = 4 wq + l / 8 (region s = k & 1, output row i = k >> 1), column l % 8; the
 // y neighbour is 16 lanes away.  Butterfly pool over the warp's 16 channels
 // 16 h ..: partners (lane ^ 1, then lane ^ 16) trade halves and keep the
 // maximum, so each lane of a window ends with channels 16 h + 4 q .. + 3,
@@ -282,21 +285,15 @@ __device__ __forceinline__ void conv2_epilogue(uint32_t taddr, unsigned char* ac
 __device__ __forceinline__ void conv3_epilogue(uint32_t taddr, unsigned char* feat_pair, const float* cb, int warp,
                                                int lane) {
   const int h = warp >> 2, wq = warp & 3;
-  uint32_t lo0[8], hi0[8], lo1[8], hi1[8], lo2[8], hi2[8];
-  tmem_ld8_nw(taddr + 16 * h, lo0);
-  tmem_ld8_nw(taddr + 16 * h + 8, hi0);
-  tmem_ld8_nw(taddr + 32 + 16 * h, lo1);
-  tmem_ld8_nw(taddr + 32 + 16 * h + 8, hi1);
-  tmem_ld8_nw(taddr + 64 + 16 * h, lo2);
-  tmem_ld8_nw(taddr + 64 + 16 * h + 8, hi2);
-  tmem_wait_ld(lo0, hi0, lo1, hi1);
-  tmem_wait_ld(lo2, hi2, lo0, hi0);        // all loads are complete; ties the last two
+  uint32_t lo[8], hi[8], unused0[8], unused1[8];
+  tmem_ld8_nw(taddr + 16 * h, lo);
+  tmem_ld8_nw(taddr + 16 * h + 8, hi);
+  tmem_wait_ld(lo, hi, unused0, unused1);
   const bool xo = lane & 1, yo = (lane & 16) != 0;
   float v[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const float a = (__uint_as_float(lo0[c]) + __uint_as_float(lo1[c])) + __uint_as_float(lo2[c]);
-    const float b = (__uint_as_float(hi0[c]) + __uint_as_float(hi1[c])) + __uint_as_float(hi2[c]);
+    const float a = __uint_as_float(lo[c]), b = __uint_as_float(hi[c]);
     v[c] = fmaxf(xo ? b : a, __shfl_xor_sync(0xffffffffu, xo ? a : b, 1));
   }
 #pragma unroll
@@ -454,7 +451,7 @@ template <typename InT>
 __global__ void __launch_bounds__(kBlockT, 1) cnn_infer_tc_kernel(const InferArgs a, int* __restrict__ err,
                                                                    long long wait_limit) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar1[4];     // conv1 tile (region, tile) of a pair done
+  __shared__ __align__(8) uint64_t bar1;        // conv1 of a pair done
   __shared__ __align__(8) uint64_t bar2, bar3;  // conv2 / conv3 of a pair done
   __shared__ __align__(8) uint64_t e_full[2], e_empty[2];   // expanded-map slots staged / read
   __shared__ __align__(8) uint64_t c1_done, c2_done, c3_done;   // epilogues done (accumulators free, maps written)
@@ -484,7 +481,7 @@ __global__ void __launch_bounds__(kBlockT, 1) cnn_infer_tc_kernel(const InferArg
   }
   if (warp == 0) tmem_alloc(&tmem_base, kTmemColsT);
   if (tid == 0) {
-    for (int j = 0; j < 4; ++j) mbar_init(&bar1[j], 1);
+    mbar_init(&bar1, 1);
     mbar_init(&bar2, 1);
     mbar_init(&bar3, 1);
     for (int j = 0; j < 2; ++j) {
@@ -509,17 +506,22 @@ __global__ void __launch_bounds__(kBlockT, 1) cnn_infer_tc_kernel(const InferArg
   if (warp >= kProducerWarp0) {
     // staging: expanded maps of pair k into slot k % 2, once conv1 of pair k - 2 has read it;
     // warp p does half p % 2 of region p / 2
-    const int pw = warp - kProducerWarp0, rs = pw >> 1, half = pw & 1;
-    int px[kStageRows];
-    load_half_region<InT>(a, pair_region(a, 0, rs), half, lane, px);
+    const int rs = warp - kProducerWarp0;
+    int px0[kStageRows], px1[kStageRows];
+    load_half_region<InT>(a, pair_region(a, 0, rs), 0, lane, px0);
+    load_half_region<InT>(a, pair_region(a, 0, rs), 1, lane, px1);
     for (long long k = 0; k < pairs; ++k) {
       const int slot = static_cast<int>(k & 1);
       if (k >= 2 && !wait_or_abort(&e_empty[slot], static_cast<uint32_t>(((k - 2) >> 1) & 1), wait_limit, abort)) break;
-      store_half_expanded(px, half, sm + kTE + (2 * slot + rs) * kEBytes, lane);
+      store_half_expanded(px0, 0, sm + kTE + (2 * slot + rs) * kEBytes, lane);
+      store_half_expanded(px1, 1, sm + kTE + (2 * slot + rs) * kEBytes, lane);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&e_full[slot]);
-      if (k + 1 < pairs) load_half_region<InT>(a, pair_region(a, k + 1, rs), half, lane, px);
+      if (k + 1 < pairs) {
+        load_half_region<InT>(a, pair_region(a, k + 1, rs), 0, lane, px0);
+        load_half_region<InT>(a, pair_region(a, k + 1, rs), 1, lane, px1);
+      }
     }
   } else if (warp == kIssuerWarp) {
     // MMA issue: iteration k issues conv1 of pair k, conv2 of pair k - 1, conv3 of pair k - 2
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(kBlockT, 1) cnn_infer_tc_kernel(const InferArg
             umma_bf16(tmem + kC1Col + 64 * q,
                       umma_desc(e_s + (2 * slot + (q >> 1)) * kEBytes + (q & 1) * 8 * kERow, kERow, 128),
                       umma_desc(b1_s, 128, 256), idesc64, 0u);
-            umma_commit(&bar1[q]);
+            if (q == 3) umma_commit(&bar1);
           }
           umma_commit(&e_empty[slot]);
         }
@@ -574,14 +576,13 @@ __global__ void __launch_bounds__(kBlockT, 1) cnn_infer_tc_kernel(const InferArg
         if (k >= 3 && !wait_or_abort(&c3_done, static_cast<uint32_t>((k - 3) & 1), wait_limit, abort)) break;
         tc_fence_after();
         if (lane == 0) {
-          // conv3 of pair k - 2: 9 taps x 2 channel halves of K = 16, N = 32, K-step j into partial sum j % 3
+          // conv3 of pair k - 2: 9 taps x 2 channel halves of K = 16, N = 32
           const uint32_t m2 = act2_s + static_cast<uint32_t>(k & 1) * kAct2T;
 #pragma unroll
           for (int j = 0; j < 18; ++j) {
             const int tap = j >> 1, h = j & 1;
-            umma_bf16(tmem + kC3Col + 32 * (j % 3),
-                      umma_desc(m2 + ((tap / 3) * 20 + tap % 3) * 16 + 2 * h * kA3Plane, kA3Plane, 160),
-                      umma_desc(b3_s + j * 1024, 128, 256), idesc32, j >= 3 ? 1u : 0u);
+            umma_bf16(tmem + kC3Col, umma_desc(m2 + ((tap / 3) * 20 + tap % 3) * 16 + 2 * h * kA3Plane, kA3Plane, 160),
+                      umma_desc(b3_s + j * 1024, 128, 256), idesc32, j > 0 ? 1u : 0u);
           }
           umma_commit(&bar3);
         }
@@ -600,12 +601,9 @@ __global__ void __launch_bounds__(kBlockT, 1) cnn_infer_tc_kernel(const InferArg
     for (long long k = 0; k < pairs + 2; ++k) {
       if (k < pairs) {
         unsigned char* m1 = sm + kTAct1 + (k & 1) * kAct1T;
-#pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-          ok &= wait_or_abort(&bar1[q], static_cast<uint32_t>(k & 1), wait_limit, abort);
-          tc_fence_after();
-          conv1_epilogue(tmem + wl + kC1Col + 64 * q, m1, q >> 1, q & 1, cb, warp, lane);
-        }
+        ok &= wait_or_abort(&bar1, static_cast<uint32_t>(k & 1), wait_limit, abort);
+        tc_fence_after();
+        conv1_epilogue(tmem + wl + kC1Col, m1, cb, warp, lane);
         fence_proxy_async_smem();             // the conv2 input map is read by the tensor cores
         tc_fence_before();
         __syncwarp();
