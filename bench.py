@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rd-speedup", action="store_true",
+                    help="skip the learned-decision speed-up sub-record of the default line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run every transform with its default pipeline schedule")
     ap.add_argument("--pass", dest="pass_", default="N32_hat",
@@ -494,6 +496,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = frames_cpu_baseline(luma_h, args.cpu_seconds)
 
+    # ---- learned-decision speed-up sub-record (rank 0, one GPU only) ----------
+    rd_speedup = None
+    if rank == 0 and world == 1 and not args.no_rd_speedup:
+        rd_speedup = rd_speedup_record(dev)
+
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -513,6 +520,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": step.launches_per_step * args.steps,
         "clocks": clock,
+        "rd_speedup": rd_speedup,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -903,6 +911,75 @@ def train_selector(args, dev):
     net.pack()
     return dict(qs=qs, slots=slots, n=n, regs=regs, regs_p=regs_p, search=search, labels_ex=labels_ex, n_train=n_train,
                 net=net, losses=losses, train_ms=train_ms, total=total, B=B, gen_s=gen_s, stream=stream)
+
+
+def rd_speedup_record(dev, n_regions=100_000, epochs=12, reps=5, fracs=(0.25, 0.4, 0.5, 0.6)):
+    """Bounded learned-decision sub-record of the default line (outside its timed
+    region): a selector trained on the first 90 % of n_regions synthetic 32 x 32
+    regions (train_selector), then, over all regions at q = 8, 16, 32, the
+    exhaustive search against the learned decision (network, then exhaustive
+    re-decision of the regions whose smallest margin is below tau; tau a
+    quantile of the training regions' margins), each timed with CUDA events.
+    The reported fallback share is the smallest of `fracs` that keeps the
+    held-out RD-cost increase within 1 %."""
+    import types
+    import torch
+    from paper_2207_11638_gb300 import binding as b
+    t0 = time.time()
+    t = train_selector(types.SimpleNamespace(regions=n_regions, epochs=epochs, lr=2e-3, mu=300.0), dev)
+    qs, slots, n, regs, search, net, n_train = t["qs"], t["slots"], t["n"], t["regs"], t["search"], t["net"], \
+        t["n_train"]
+    stream = t["stream"]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps
+
+    lab_ex = search.search(regs, qs)
+    j_ex = _j_float(search.evaluate(regs, qs, lab_ex)[0])
+    held = slice(n_train, n)
+    _, mg = net.infer(regs, slots, margin=True)
+    mmin = mg[:, :n_train].min(dim=0).values.float()
+    sample = mmin[torch.randperm(n_train, device=dev)[:200_000]]
+    ms_search = timed(lambda: search.search(regs, qs))
+    ms_cnn = timed(lambda: net.infer(regs, slots, margin=True))
+    rows = []
+    for frac in fracs:
+        tau = float(torch.quantile(sample, frac))
+        out = {}
+
+        def decide(tau=tau):
+            lab, m = net.infer(regs, slots, margin=True)
+            idx, cnt = b.cnn_select(m, tau)
+            search.search_subset(regs, qs, idx, cnt, lab)
+            out["lab"], out["cnt"] = lab, cnt
+
+        ms = timed(decide)
+        j = _j_float(search.evaluate(regs, qs, out["lab"])[0])
+        inc = 100.0 * float(j[:, held].sum() / j_ex[:, held].sum() - 1.0)
+        rows.append({"fallback_frac": frac, "regions_searched": int(out["cnt"].cpu()[0]), "decision_ms": round(ms, 3),
+                     "speedup_vs_search": round(ms_search / ms, 3), "rd_cost_increase_pct_heldout": round(inc, 3)})
+    b.check_device()
+    ok = [r for r in rows if r["rd_cost_increase_pct_heldout"] <= 1.0]
+    head = ok[0] if ok else None
+    return {
+        "what": "learned quadtree decision vs exhaustive RD search (32x32 regions, T^ 8/16/32, q 8/16/32)",
+        "regions": n, "train_regions": n_train, "heldout_regions": n - n_train, "epochs": epochs,
+        "training_ms": round(t["train_ms"], 1), "exhaustive_ms": round(ms_search, 3),
+        "cnn_only_ms": round(ms_cnn, 3),
+        "learned_ms": head["decision_ms"] if head else None,
+        "fallback_frac": head["fallback_frac"] if head else None,
+        "rd_cost_increase_pct_heldout": head["rd_cost_increase_pct_heldout"] if head else None,
+        "speedup_vs_search": head["speedup_vs_search"] if head else None,
+        "sweep": rows, "wall_s": round(time.time() - t0, 1),
+    }
 
 
 def run_learned(args):
