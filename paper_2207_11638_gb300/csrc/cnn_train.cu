@@ -234,20 +234,39 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const uint16_t* __restrict__
     }
 }
 
-// out[co * kreal + k] = sum over chunks of part[chunk][co][k] for k < kreal; bias likewise
-__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ part_b, int chunks,
-                                    int co_n, int K, int kreal, float* __restrict__ gw, float* __restrict__ gb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < co_n * kreal) {
-    const int co = i / kreal, k = i - co * kreal;
-    float s = 0.f;
-    for (int c = 0; c < chunks; ++c) s += part[(static_cast<long long>(c) * co_n + co) * K + k];
-    gw[i] = s;
-  } else if (gb != nullptr && i < co_n * kreal + co_n) {
-    const int co = i - co_n * kreal;
-    float s = 0.f;
-    for (int c = 0; c < chunks; ++c) s += part_b[c * co_n + co];
-    gb[co] = s;
+// out[co * kreal + k] = sum over chunks of part[chunk][co][k] for k < kreal; bias likewise.
+// A CTA of 32 warps owns 32 consecutive outputs (lane = output, so loads are
+// coalesced along k); warp w sums chunks w, w + 32, w + 64, ... in that order,
+// then warp 0 adds the 32 warps' sums in warp order: a fixed order, so the
+// result is the same bit for bit on every run.
+constexpr int kReduceWarps = 32;
+__global__ void __launch_bounds__(32 * kReduceWarps) wgrad_reduce_kernel(const float* __restrict__ part,
+                                                                         const float* __restrict__ part_b, int chunks,
+                                                                         int co_n, int K, int kreal,
+                                                                         float* __restrict__ gw, float* __restrict__ gb) {
+  __shared__ float red[kReduceWarps][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_w = co_n * kreal, n_out = n_w + (gb != nullptr ? co_n : 0);
+  const int e = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (e < n_w) {
+    const int co = e / kreal, k = e - co * kreal;
+    const float* p = part + static_cast<long long>(co) * K + k;
+    const long long step = static_cast<long long>(co_n) * K;
+#pragma unroll 4
+    for (int c = warp; c < chunks; c += kReduceWarps) s += p[c * step];
+  } else if (e < n_out) {
+    const int co = e - n_w;
+#pragma unroll 4
+    for (int c = warp; c < chunks; c += kReduceWarps) s += part_b[c * co_n + co];
+  }
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && e < n_out) {
+    float t = red[0][lane];
+    for (int w = 1; w < kReduceWarps; ++w) t += red[w][lane];
+    if (e < n_w) gw[e] = t;
+    else gb[e - n_w] = t;
   }
 }
 
@@ -265,7 +284,7 @@ int wgrad_launch_t(const uint16_t* dZ, const uint16_t* A, long long M, int K, in
   e = cudaGetLastError();
   if (e != cudaSuccess) return static_cast<int>(e);
   const int total = CO * kreal + (gb ? CO : 0);
-  wgrad_reduce_kernel<<<(total + 255) / 256, 256, 0, s>>>(part, part_b, chunks, CO, K, kreal, gw, gb);
+  wgrad_reduce_kernel<<<(total + 31) / 32, 32 * kReduceWarps, 0, s>>>(part, part_b, chunks, CO, K, kreal, gw, gb);
   return static_cast<int>(cudaGetLastError());
 }
 
