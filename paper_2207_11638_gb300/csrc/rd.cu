@@ -59,18 +59,40 @@ __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
   return (static_cast<u128>(hi) << 64) | lo;
 }
 
-// round(B / q) for B = y s_i / (n s_j), decided exactly (see the file comment).
-// `unit` = n^2 q^2 d_i; `est` = sqrt(d_j) / (n q sqrt(d_i)) in float gives a
-// first guess within one of the answer, which the integer tests then settle.
-__device__ __forceinline__ int quant_level(int y, unsigned dj, unsigned long long unit, float est) {
-  const unsigned a = static_cast<unsigned>(y < 0 ? -y : y);
-  if (a == 0) return 0;
+// The level's magnitude from the float estimate alone, where that is safe.
+// With x = |y| sqrt(d_j) / (n q sqrt(d_i)) the level is floor(x + 1/2).  t =
+// fmaf(float(|y|), est, 1/2) carries seven correctly rounded operations
+// (sqrtf twice, two products, the reciprocal, the conversion of |y| and the
+// fma), so |t - (x + 1/2)| <= 7.01 * 2^-24 (x + 1/2) < 2^-21 t (1 + 2^-20).  If
+// t - d and t + d, d = t 2^-20, round down to one integer, floor(t) is the
+// level; otherwise `exact` is set and the integer test must decide.
+__device__ __forceinline__ int quant_guess(unsigned a, float est, bool& exact) {
+  const float t = fmaf(static_cast<float>(a), est, 0.5f);
+  const float d = t * 0x1p-20f;
+  const float lo = floorf(t - d);
+  exact = lo != floorf(t + d);
+  return static_cast<int>(lo);
+}
+
+// The level's magnitude by the integer test, from a guess within one of it
+__device__ __forceinline__ int quant_settle(unsigned a, unsigned dj, unsigned long long unit, int k) {
   const unsigned long long lhs = (static_cast<unsigned long long>(a) * a) * (4ull * dj);
-  int k = __float2int_rd(fmaf(static_cast<float>(a), est, 0.5f));
   if (k < 0) k = 0;
   while (static_cast<unsigned long long>(2 * k + 1) * static_cast<unsigned>(2 * k + 1) * unit <= lhs) ++k;
   while (k > 0 && static_cast<unsigned long long>(2 * k - 1) * static_cast<unsigned>(2 * k - 1) * unit > lhs) --k;
-  return y < 0 ? -k : k;
+  return k;
+}
+
+// Key of zig-zag position (i, j) of an n x n block that orders like the
+// position itself: 64 (i + j) + (i on odd diagonals, 63 - i on even ones), as
+// zig-zag runs down odd diagonals and up even ones.  key_pos inverts it.
+__device__ __forceinline__ int zz_key_even_j(int i) { return 64 * i + ((i & 1) ? i : 63 - i); }
+__device__ __forceinline__ int zz_key_odd_j(int i) { return 64 * i + ((i & 1) ? 63 - i : i); }
+__device__ __forceinline__ int key_pos(int n, int key) {
+  if (key < 0) return -1;
+  const int d = key >> 6, sub = key & 63;
+  const int i = (d & 1) ? sub : 63 - sub;
+  return zigzag_pos(n, i, d - i);
 }
 
 __device__ __forceinline__ int level_bits(int l) {
@@ -162,17 +184,24 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
     int rate[S], last[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) { rate[s] = 0; last[s] = -1; }
-    // quantise, count bits, dequantise (row `lane`)
+    const int key_e = zz_key_even_j(i), key_o = zz_key_odd_j(i);
+    // quantise, count bits, dequantise (row `lane`); last[] holds zig-zag keys here
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const int j = c % N;
-      const int l = quant_level(y[c], static_cast<unsigned>(dd[j]), unit, sdj[j] * est_i);
-      if (l != 0) {
-        rate[c / N] += level_bits(l);
-        last[c / N] = max(last[c / N], zigzag_pos(N, i, j));
+      const unsigned a = static_cast<unsigned>(y[c] < 0 ? -y[c] : y[c]);
+      bool exact;
+      int k = quant_guess(a, sdj[j] * est_i, exact);
+      if (__any_sync(0xffffffffu, exact)) {       // warp-uniform: rare
+        if (exact) k = quant_settle(a, static_cast<unsigned>(dd[j]), unit, k);
       }
+      const int l = y[c] < 0 ? -k : k;
+      rate[c / N] += level_bits(k);
+      if (k != 0) last[c / N] = max(last[c / N], ((j & 1) ? key_o : key_e) + 64 * j);
       // |N q L| < 2^23 and c < 2^16: one 32 x 32 -> 64-bit product
-      buf[lane * kPitch + c] = static_cast<long long>(N * q * l) * cc[i * (N + 1) + j];
+      long long yq = 0;
+      if (k != 0) yq = static_cast<long long>(N * q * l) * cc[i * (N + 1) + j];
+      buf[lane * kPitch + c] = yq;
     }
     __syncwarp();
     // inverse, columns: (2U) Y'
@@ -194,9 +223,12 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
     }
     __syncwarp();
     // inverse, rows: ((2U) Y') T = 2 Z'; squared error against 2^F N^2 A
+    // squared errors below 2^58 are summed in 64 bits (at most 32 of them per
+    // segment: below 2^63), larger ones in 128 bits
     u128 dist[S];
+    unsigned long long dsmall[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) dist[s] = 0;
+    for (int s = 0; s < S; ++s) dist[s] = 0, dsmall[s] = 0;
     {
       long long row[32];
 #pragma unroll
@@ -214,12 +246,14 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
           const long long e = ref - (x[k] >> 1);              // 2Z' is even: exact
           const unsigned long long ae = static_cast<unsigned long long>(e < 0 ? -e : e);
           if (lane < vrows && c < vcols) {
-            if (ae >> 32) dist[s] += static_cast<u128>(ae) * ae;
-            else dist[s] += static_cast<unsigned long long>(static_cast<unsigned>(ae)) * static_cast<unsigned>(ae);
+            if (ae >> 29) dist[s] += static_cast<u128>(ae) * ae;
+            else dsmall[s] += static_cast<unsigned long long>(static_cast<unsigned>(ae)) * static_cast<unsigned>(ae);
           }
         }
       }
     }
+#pragma unroll
+    for (int s = 0; s < S; ++s) dist[s] += dsmall[s];
     __syncwarp();
     // per block: sum over its N lanes (aligned groups), then the cost
 #pragma unroll
@@ -238,7 +272,7 @@ __device__ __forceinline__ void rd_size(const RdKernelArgs& ka, const RdSmem& sm
       const int br = lane / N;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const int bits = 1 + (last[s] + 1) + rate[s];
+        const int bits = 1 + (key_pos(N, last[s]) + 1) + rate[s];
         cost[qi][cost_base(N) + br * S + s] = dist[s] * kScale + lam * static_cast<unsigned>(bits);
         if (edist != nullptr) {
           edist[qi][cost_base(N) + br * S + s] = dist[s] * kScale;
