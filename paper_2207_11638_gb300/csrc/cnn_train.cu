@@ -15,6 +15,7 @@
 //                      channel-transposed W_l (a 3 x 3 correlation's adjoint)
 // Weight gradients are summed per chunk of rows into partial buffers, then
 // reduced in a fixed order, so a step is reproducible bit for bit.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,116 +34,255 @@ using namespace cnn;
 // ---------------------------------------------------------------------------
 // GEMM  C[M][N] = A[M][K] B[N][K]^T on the tcgen05 tensor cores (bf16 in,
 // float32 accumulate in tensor memory).  K % 16 == 0, N a multiple of BN
-// (16, 32 or 64); rows of A beyond M read as zero.  A CTA of 4 warps owns a
-// 128 x BN tile:
-//   1. all threads copy the A tile (128 x K) and the B tile (BN x K) into
-//      shared memory in the no-swizzle K-major core-matrix layout, one slab
-//      per MMA (K = 16): element (r, k) of slab s = k / 16 sits at
-//      s * rows * 32 + (r / 8) * 256 + ((k / 8) % 2) * 128 + (r % 8) * 16 + (k % 8) * 2
-//      bytes, i.e. core matrices 128 B apart along K and 256 B apart along
-//      M / N; then they are fenced for the async proxy;
-//   2. one thread issues the K/16 MMAs into a 128 x BN float32 accumulator in
-//      tensor memory and commits them to an mbarrier;
-//   3. after a bounded wait, warp w loads accumulator lanes 32w .. 32w + 31
-//      (rows of the tile) and applies the epilogue: float32 out, or
-//      bias + ReLU -> bf16.
+// (16, 32 or 64); rows of A beyond M read as zero.  A persistent CTA owns a
+// column block of BN and walks the 128-row tiles t = blockIdx.x + i gridDim.x:
+//   * B (BN x K) is copied into shared memory once, in the no-swizzle K-major
+//     core-matrix layout: slab kk (K = 16) at kk * BN * 32 bytes, core matrices
+//     128 B apart along K and 256 B apart along N;
+//   * A arrives by TMA (cp.async.bulk.tensor through a tensor map of this GPU's
+//     A[M][K]) in a ring of 4 stages of 64 K: one box of 8 K x 128 rows per
+//     copy, so a stage holds chunk c of 8 K at c * 2048 + row * 16 bytes:
+//     core matrices 2048 B apart along K and 128 B apart along M;
+//   * one thread issues the copies (running up to 3 stages ahead) and the
+//     MMAs, 4 per stage, into one of two tensor-memory accumulators;
+//     tcgen05.commit frees a stage when its MMAs are done and publishes a tile
+//     when its last MMA is;
+//   * 4 epilogue warps drain a tile's accumulator (warp w: lanes 32w ..), hand
+//     it back, and store: float32 out, or bias + ReLU -> bf16.
+// So the copies of the next tiles, the MMAs of this one and the epilogue of
+// the previous one overlap.  Every wait is bounded; a role that gives up
+// raises a shared flag that ends the others' waits, the issuing thread waits
+// (bounded) for its copies and MMAs in flight, and the CTA records the error
+// word and frees its tensor memory.
 // ---------------------------------------------------------------------------
-constexpr int kGemmThreads = 128;
+constexpr int kGemmKS = 64;                        // K per pipeline stage
+constexpr int kGemmStages = 4;
+constexpr int kGemmStageBytes = 128 * kGemmKS * 2;
+constexpr int kGemmEpiWarps = 4;
+constexpr int kGemmThreads = 32 * (kGemmEpiWarps + 1);
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// wait for phase `parity`; false once the CTA has given up (the shared flag) or
+// after about `limit` SM cycles, which also raises the flag
+__device__ __forceinline__ bool gemm_wait(uint64_t* bar, uint32_t parity, long long limit, volatile int* abort) {
+  if (mbar_try_wait(bar, parity, 2000u)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity, 2000u)) {
+    if (*abort) return false;
+    if (clock64() - t0 > limit) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
 
 // `skip_mma` (failure-detection test): issue neither the MMAs nor their
-// commit, so that the accumulator wait runs out with nothing in flight.
+// commits, so that the waits run out with nothing but finished copies behind them.
 template <int BN, bool RELU_BF16>
-__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const uint16_t* __restrict__ A,
-                                                               const uint16_t* __restrict__ B, long long M, int N,
-                                                               int K, const float* __restrict__ bias,
-                                                               void* __restrict__ C, int* __restrict__ err,
-                                                               long long wait_limit, int skip_mma) {
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                  const uint16_t* __restrict__ B, long long M, int N,
+                                                                  int K, const float* __restrict__ bias,
+                                                                  void* __restrict__ C, int* __restrict__ err,
+                                                                  long long wait_limit, int skip_mma) {
   extern __shared__ __align__(1024) unsigned char smg[];
-  __shared__ __align__(8) uint64_t done;
+  __shared__ __align__(8) uint64_t full[kGemmStages], empty[kGemmStages], acc_full[2], acc_free[2], fin;
   __shared__ uint32_t tmem_base;
-  constexpr uint32_t kCols = BN < 32 ? 32 : BN;
-  constexpr uint32_t kSlabA = 128 * 32, kSlabB = BN * 32;   // bytes per K = 16 slab
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+  constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
+  constexpr uint32_t kSlabB = BN * 32;             // bytes per K = 16 slab of B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long m0 = static_cast<long long>(blockIdx.x) * 128;
   const int n0 = blockIdx.y * BN;
-  unsigned char* sa = smg;
-  unsigned char* sb = smg + static_cast<size_t>(K) * 128 * 2;
-  const int kc_n = K / 8;
-  for (int i = tid; i < kc_n * 128; i += kGemmThreads) {
-    const int kc = i >> 7, r = i & 127;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (m0 + r < M) v = *reinterpret_cast<const uint4*>(A + (m0 + r) * K + kc * 8);
-    *reinterpret_cast<uint4*>(sa + (kc >> 1) * kSlabA + (r >> 3) * 256 + (kc & 1) * 128 + (r & 7) * 16) = v;
-  }
-  for (int i = tid; i < kc_n * BN; i += kGemmThreads) {
+  const int ks_per_tile = (K + kGemmKS - 1) / kGemmKS;
+  const long long n_tiles = (M + 127) / 128;
+  const long long my_tiles = (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  unsigned char* sb = smg;
+  unsigned char* sa = smg + (BN * K * 2 + 1023) / 1024 * 1024;
+  for (int i = tid; i < (K / 8) * BN; i += kGemmThreads) {
     const int kc = i / BN, r = i - kc * BN;
     *reinterpret_cast<uint4*>(sb + (kc >> 1) * kSlabB + (r >> 3) * 256 + (kc & 1) * 128 + (r & 7) * 16) =
         *reinterpret_cast<const uint4*>(B + static_cast<long long>(n0 + r) * K + kc * 8);
   }
-  fence_proxy_async_smem();                // the copies above are read by the tensor cores
+  fence_proxy_async_smem();                // B is read by the tensor cores
   if (warp == 0) tmem_alloc(&tmem_base, kCols);
   if (tid == 0) {
-    mbar_init(&done, 1);
+    for (int j = 0; j < kGemmStages; ++j) {
+      mbar_init(&full[j], 1);
+      mbar_init(&empty[j], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&acc_full[j], 1);
+      mbar_init(&acc_free[j], kGemmEpiWarps);
+    }
+    mbar_init(&fin, 1);
+    abort_flag = 0;
     fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  if (tid == 0 && !skip_mma) {
-    constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
-    const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
-    for (int kk = 0; kk < K / 16; ++kk)
-      umma_bf16(tmem, umma_desc(a0 + kk * kSlabA, 128, 256), umma_desc(b0 + kk * kSlabB, 128, 256), idesc,
-                kk > 0 ? 1u : 0u);
-    umma_commit(&done);
-  }
-  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&done, 0, wait_limit));
-  tc_fence_after();
-  if (ok) {
-    const long long row = m0 + warp * 32 + lane;
+  if (warp == kGemmEpiWarps) {
+    if (lane == 0) {
+      // copies of stage g run kGemmStages - 1 stages ahead of the MMAs of stage g - (kGemmStages - 1)
+      constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
+      const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+      const long long total = my_tiles * ks_per_tile;
+      long long issued = 0;                        // stages whose copies were issued
+      bool ok = true;
+      for (long long g = 0; g < total + kGemmStages - 1; ++g) {
+        if (g < total) {
+          const int st = static_cast<int>(g % kGemmStages);
+          const long long use = g / kGemmStages;
+          if (use >= 1 && !gemm_wait(&empty[st], static_cast<uint32_t>((use - 1) & 1), wait_limit, abort)) {
+            ok = false;
+            break;
+          }
+          const long long tile = blockIdx.x + (g / ks_per_tile) * gridDim.x;
+          const int k0 = static_cast<int>(g % ks_per_tile) * kGemmKS, kn = min(kGemmKS, K - k0);
+          mbar_arrive_expect_tx(&full[st], static_cast<uint32_t>(kn / 8) * 2048u);
+          for (int c = 0; c < kn / 8; ++c)
+            tma_load_2d(sa + st * kGemmStageBytes + c * 2048, &tmA, k0 + 8 * c, static_cast<int>(tile * 128),
+                        &full[st]);
+          issued = g + 1;
+        }
+        const long long ci = g - (kGemmStages - 1);
+        if (ci >= 0) {
+          const int st = static_cast<int>(ci % kGemmStages);
+          const long long ti = ci / ks_per_tile;
+          const int s = static_cast<int>(ci % ks_per_tile), b = static_cast<int>(ti & 1);
+          if (!gemm_wait(&full[st], static_cast<uint32_t>((ci / kGemmStages) & 1), wait_limit, abort) ||
+              (s == 0 && ti >= 2 &&
+               !gemm_wait(&acc_free[b], static_cast<uint32_t>(((ti - 2) >> 1) & 1), wait_limit, abort))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (!skip_mma) {
+            const int k0 = s * kGemmKS, kn = min(kGemmKS, K - k0);
+            for (int kk = 0; kk < kn / 16; ++kk)
+              umma_bf16(tmem + b * BN, umma_desc(a0 + st * kGemmStageBytes + 2 * kk * 2048, 2048, 128),
+                        umma_desc(b0 + (k0 / 16 + kk) * kSlabB, 128, 256), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(&empty[st]);
+            if (s == ks_per_tile - 1) umma_commit(&acc_full[b]);
+          }
+        }
+      }
+      if (!ok) *abort = 1;
+      // nothing may still write this CTA's memory when it exits: the MMAs issued
+      // (one commit tracks them all) and the copies issued (each stage's last)
+      umma_commit(&fin);
+      (void)mbar_wait_bounded(&fin, 0u, wait_limit);
+      for (long long g = issued - 1; g >= 0 && g >= issued - kGemmStages; --g)
+        (void)mbar_wait_bounded(&full[g % kGemmStages], static_cast<uint32_t>((g / kGemmStages) & 1), wait_limit);
+    }
+    __syncwarp();
+  } else {
+    for (long long ti = 0; ti < my_tiles; ++ti) {
+      const int b = static_cast<int>(ti & 1);
+      const bool ok = __all_sync(0xffffffffu, gemm_wait(&acc_full[b], static_cast<uint32_t>((ti >> 1) & 1),
+                                                        wait_limit, abort));
+      if (!ok) break;
+      tc_fence_after();
+      float v[BN];
 #pragma unroll
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+      for (int c0 = 0; c0 < BN; c0 += 16)
+        tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + b * BN + c0,
+                  *reinterpret_cast<float(*)[16]>(v + c0));
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_free[b]);   // the accumulator is free for tile ti + 2
+      const long long row = (blockIdx.x + ti * gridDim.x) * 128 + warp * 32 + lane;
       if (row < M) {
-        const int col = n0 + c0;
-        if (RELU_BF16) {
-          uint32_t w[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            w[j] = pack_bf16(fmaxf(v[2 * j] + bias[col + 2 * j], 0.f), fmaxf(v[2 * j + 1] + bias[col + 2 * j + 1], 0.f));
-          uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(C) + row * N + col);
-          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-        } else {
-          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(C) + row * N + col);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          const int col = n0 + c0;
+          if (RELU_BF16) {
+            uint32_t w[8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            for (int j = 0; j < 8; ++j)
+              w[j] = pack_bf16(fmaxf(v[c0 + 2 * j] + bias[col + 2 * j], 0.f),
+                               fmaxf(v[c0 + 2 * j + 1] + bias[col + 2 * j + 1], 0.f));
+            uint4* dst = reinterpret_cast<uint4*>(static_cast<uint16_t*>(C) + row * N + col);
+            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          } else {
+            float4* dst = reinterpret_cast<float4*>(static_cast<float*>(C) + row * N + col);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              dst[j] = make_float4(v[c0 + 4 * j], v[c0 + 4 * j + 1], v[c0 + 4 * j + 2], v[c0 + 4 * j + 3]);
+          }
         }
       }
     }
-  } else if (tid == 0) {
-    atomicOr(err, 2);
-    // the MMAs may still be running: wait for them (bounded) before freeing their memory
-    (void)mbar_wait_bounded(&done, 0, wait_limit);
   }
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && abort_flag) atomicOr(err, 2);
   if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// cuTensorMapEncodeTiled, fetched from the driver once (no link-time dependency on it)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+int sm_count() {
+  static int n[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (n[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    n[dev] = v;
+  }
+  return n[dev];
 }
 
 template <int BN, bool RELU_BF16>
 int gemm_launch_t(const uint16_t* A, const uint16_t* B, long long M, int N, int K, const float* bias, void* C,
                   int* err, cudaStream_t s) {
-  const int smem = (128 + BN) * K * 2;
+  EncodeTiledFn enc = encode_tiled();
+  const int sms = sm_count();
+  if (enc == nullptr || sms <= 0) return static_cast<int>(cudaErrorNotSupported);
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(M)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(K) * 2};
+  const cuuint32_t box[2] = {8, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(A), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return static_cast<int>(cudaErrorInvalidValue);
+  const int smem = (BN * K * 2 + 1023) / 1024 * 1024 + kGemmStages * kGemmStageBytes;
   auto kern = gemm_tc_kernel<BN, RELU_BF16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return static_cast<int>(e);
-  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>(N / BN));
+  const long long tiles = (M + 127) / 128;
+  const int cols = N / BN;
+  const long long want = (sms + cols - 1) / cols;   // about one CTA per SM over the column blocks
+  dim3 grid(static_cast<unsigned>(tiles < want ? tiles : want), static_cast<unsigned>(cols));
   long long limit = kDefaultWaitLimit;
   const int mode = fault_mode(&limit);
-  kern<<<grid, kGemmThreads, smem, s>>>(A, B, M, N, K, bias, C, err, limit, (mode & 2) ? 1 : 0);
+  kern<<<grid, kGemmThreads, smem, s>>>(map, B, M, N, K, bias, C, err, limit, (mode & 2) ? 1 : 0);
   return static_cast<int>(cudaGetLastError());
 }
 
