@@ -61,7 +61,7 @@ typedef enum {
   CDCT_ENOMEM = 2,        /* host allocation failed */
   CDCT_ECUDA = 3,         /* a CUDA launch or call failed */
   CDCT_EUNSUPPORTED = 4,  /* valid but not provided (e.g. EXACT with N != 8) */
-  CDCT_ETIMEOUT = 5       /* reserved for bounded device waits */
+  CDCT_ETIMEOUT = 5       /* a bounded device wait gave up (reported by cdct_check_device) */
 } cdct_status;
 
 typedef enum {
