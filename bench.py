@@ -34,10 +34,11 @@ UNIT = "Gpixel/s"
 BYTES_PER_PX = 2 + 4          # int16 residual in, float32 reconstruction out
 FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum per pixel of the fused kernel,
-# from the committed ncu capture of the 16-frame luma launch (the mean of
-# N = 8, 16, 32: 4.18, 4.21, 4.24 B/px); output lines still dirty in L2 when a
-# launch ends are written back after it and are not counted.
-NCU_TRAFFIC_BYTES_PER_PX = 4.21
+# from the committed ncu captures of the 16-frame luma launch of the current
+# kernels (the mean of N = 8, 16, 32: 4.17, 4.24, 4.19 B/px); output lines
+# still dirty in L2 when a launch ends are written back after it and are not
+# counted.
+NCU_TRAFFIC_BYTES_PER_PX = 4.20
 
 
 def parse():
