@@ -75,7 +75,8 @@ def test_oracle_sample_helpers():
     args = types.SimpleNamespace(no_cpu_baseline=False, cpu_seconds=0.0)
     regs = synth.residual_regions_32(2, seed=4)
     b = bench.rd_baseline(args, regs, (8, 16, 32), "test regions")
-    assert b["kind"] == "oracle" and b["value"] > 0 and b["sample"].startswith("1 regions of test regions")
+    assert b["kind"] == "oracle" and b["value"] > 0 and "regions of test regions" in b["sample"]
+    assert b["single_core"]["sample"].startswith("1 regions")
     args.no_cpu_baseline = True
     assert bench.rd_baseline(args, regs, (8,), "x") is None
     img = np.random.default_rng(1).integers(0, 256, (64, 96)).astype(np.uint8)
@@ -102,5 +103,15 @@ def test_all_core_oracle_baseline_states_its_cores():
     gpx, n, secs = bench.oracle_pool_sample(frames, 0.0, 2)
     assert gpx > 0 and n == 2
     cpu = bench.frames_cpu_baseline(frames, 0.0)
+    assert cpu["cores"] == cpu["nproc"] == bench.host_cores() >= 1
+    assert cpu["single_core"]["cores"] == 1 and cpu["single_core"]["value"] > 0 and cpu["value"] > 0
+
+
+def test_all_core_rd_baseline_states_its_cores():
+    from paper_2207_11638_gb300 import synth
+    regions = synth.residual_regions_32(3, seed=4)
+    gpx, n, secs = bench.oracle_rd_pool_sample(regions, (8, 16), 0.0, 2, per_task=1)
+    assert gpx > 0 and n == 2
+    cpu = bench.rd_baseline(types.SimpleNamespace(no_cpu_baseline=False, cpu_seconds=0.0), regions, (8, 16), "3 regions")
     assert cpu["cores"] == cpu["nproc"] == bench.host_cores() >= 1
     assert cpu["single_core"]["cores"] == 1 and cpu["single_core"]["value"] > 0 and cpu["value"] > 0
