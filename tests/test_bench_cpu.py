@@ -115,3 +115,9 @@ def test_all_core_rd_baseline_states_its_cores():
     cpu = bench.rd_baseline(types.SimpleNamespace(no_cpu_baseline=False, cpu_seconds=0.0), regions, (8, 16), "3 regions")
     assert cpu["cores"] == cpu["nproc"] == bench.host_cores() >= 1
     assert cpu["single_core"]["cores"] == 1 and cpu["single_core"]["value"] > 0 and cpu["value"] > 0
+
+
+def test_all_core_images_baseline():
+    imgs = [np.random.default_rng(k).integers(0, 256, (32 + 8 * k, 48)).astype(np.uint8) for k in range(3)]
+    gpx, n, secs = bench.oracle_images_pool_sample(imgs, 0.0, 2)
+    assert gpx > 0 and n == 2
